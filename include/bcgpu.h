@@ -1,0 +1,228 @@
+/*
+ * bcgpu.h -- C ABI of libbcgpu.so: incremental betweenness centrality on one GPU.
+ *
+ * The method is Nasre, Pontecorvi and Ramachandran, "Betweenness Centrality --
+ * Incremental and Faster" (arXiv 1311.2147).  The library keeps, for every ordered
+ * pair (s,t) of a graph G = (V,E) with positive integer edge weights, the distance
+ * d(s,t), the shortest-path count sigma_st (Section 2, Eq. 1 and the definition
+ * below it) and the dependency delta_s.(t) (Eq. 4), plus the BC vector (Eq. 3), all
+ * resident in device memory.  An incremental update -- a new edge, a lower edge
+ * weight (Section 1), or both on any subset of the edges incident to one vertex
+ * (Section 4) -- is applied by the rank-1 rules of Lemma 2 / Lemma 4 over the whole
+ * n x n state, after which the dependencies of the sources whose rows changed are
+ * re-accumulated by Brandes' recurrence (Eq. 4, Algorithm 1) over the shortest-path
+ * DAG rebuilt from the edges that lie on shortest paths (E*, Section 6).
+ *
+ * Conventions shared by every call:
+ *   * Vertices are 0 .. n-1.  Weights are integers >= 1 (the paper allows positive
+ *     reals; integers keep Lemma 2's tie test exact).  A graph is simple: no
+ *     self-loops and no repeated edge.
+ *   * Undirected graphs are held as G_D (Section 3, "Undirected graphs": each edge
+ *     {a,b} is the arcs (a,b) and (b,a)); their BC counts each unordered pair once,
+ *     i.e. the G_D sum halved.  Directed BC is the raw Eq. 3 sum.  No normalisation.
+ *   * Unreachable pairs: d = INF (the distance type's maximum), sigma = 0, and they
+ *     contribute nothing to BC.
+ *   * Distances are int32 (BC_DIST_I32) or int64 (BC_DIST_I64); path counts are
+ *     uint64 and overflow is detected, never wrapped; dependencies and BC are fp64.
+ *   * All pointers passed to these calls are HOST pointers unless a comment says
+ *     otherwise.  The caller owns them; the library copies what it needs before the
+ *     call returns.  The library owns all device memory of a handle until
+ *     bc_destroy.
+ *   * Every call returns a bc_status; nothing throws across the ABI.  Calls on one
+ *     handle must not overlap (the library does not lock); calls on different
+ *     handles are independent.  All work of a handle runs on the CUDA stream given to
+ *     bc_init_static (NULL = the legacy default stream).
+ *   * Device-side errors (a path count or distance that does not fit its type) are
+ *     sticky: they are reported by the call that synchronises, and the handle is
+ *     then poisoned -- every later call except bc_destroy / bc_last_error returns
+ *     BC_ERR_POISONED.
+ *   * A call rejected by host-side validation (BC_ERR_ARG, BC_ERR_NOT_INCREMENTAL)
+ *     leaves the state untouched.
+ */
+#ifndef BCGPU_H
+#define BCGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bc_graph bc_graph;   /* opaque handle */
+
+typedef enum bc_status {
+    BC_OK = 0,
+    BC_ERR_ARG = -1,             /* malformed argument or graph */
+    BC_ERR_NOT_INCREMENTAL = -2, /* new weight >= current weight of an existing edge */
+    BC_ERR_OVERFLOW = -3,        /* a path count sigma_st needs more than 64 bits */
+    BC_ERR_DIST_OVERFLOW = -4,   /* a distance does not fit the distance type */
+    BC_ERR_OOM = -5,             /* device or host allocation failed */
+    BC_ERR_CUDA = -6,            /* a CUDA runtime call failed (see bc_last_error) */
+    BC_ERR_TIMEOUT = -7,         /* a bounded device-side wait gave up */
+    BC_ERR_POISONED = -8         /* an earlier device-side error poisoned the handle */
+} bc_status;
+
+enum {
+    BC_DIRECTED = 1,
+    BC_UNDIRECTED = 2,
+    BC_DIST_I32 = 16,
+    BC_DIST_I64 = 32
+};
+
+enum { BC_UPD_EDGE = 0, BC_UPD_VERTEX = 1 };
+
+/* One incremental update of a batch (32 bytes, naturally aligned).
+ *   kind == BC_UPD_EDGE:   edge (u, v) gets weight w (a new edge or a lower weight;
+ *                          for an undirected graph the edge {u, v}).
+ *   kind == BC_UPD_VERTEX: a vertex update of v (Section 4): the k entries
+ *                          edges[first .. first + k) of the batch's bc_vedge array.
+ */
+typedef struct bc_update {
+    int32_t kind;
+    int32_t u;
+    int32_t v;
+    int32_t k;
+    int64_t w;
+    int64_t first;
+} bc_update;
+
+/* One edge of a vertex update of v: dir == 0 is the edge (x, v) (in E_i of
+ * Section 4), dir == 1 the edge (v, x) (in E_o).  dir is ignored for an undirected
+ * graph, where the edge is {v, x}.  16 bytes. */
+typedef struct bc_vedge {
+    int32_t x;
+    int32_t dir;
+    int64_t w;
+} bc_vedge;
+
+/* Per-handle counters (bc_get_info). */
+typedef struct bc_info {
+    int32_t n;
+    int32_t directed;
+    int32_t dist_bytes;          /* 4 or 8 */
+    int32_t reserved;
+    int64_t m;                   /* arcs of G (G_D for undirected) */
+    int64_t estar_arcs;          /* arcs currently held in the E* superset */
+    int64_t updates_applied;     /* updates run on the device since init */
+    int64_t rows_reaccumulated;  /* sum over updates of the sources re-accumulated */
+    int64_t noop_updates;        /* updates that changed no pair */
+    int64_t max_rows;            /* largest number of sources of one update */
+    int64_t state_bytes;         /* device bytes owned by the handle */
+    double last_init_ms;         /* device time of the static computation in bc_init_static */
+} bc_info;
+
+/*
+ * bc_init_static -- build the state of G by a static computation on the device
+ * (Brandes' algorithm, Appendix Algorithm 7: all-pairs distances and path counts,
+ * the shortest-path DAG of every source from E* as in Section 6 (Algorithm 6 steps
+ * 2-4), then Algorithm 1 for every source).  This is also the GPU full-recompute
+ * baseline.
+ *   out          receives the new handle (NULL on failure).
+ *   n            number of vertices (1 .. 65536).
+ *   m            number of edges in src/dst/w (undirected: each edge once).
+ *   src,dst,w    host arrays of m entries; w in [1, INF-1] of the distance type.
+ *   flags        exactly one of BC_DIRECTED / BC_UNDIRECTED, and one of
+ *                BC_DIST_I32 / BC_DIST_I64.
+ *   cuda_stream  a cudaStream_t (NULL = legacy default stream).
+ * Synchronous.  Returns BC_ERR_ARG for a malformed graph or flags, BC_ERR_OOM when
+ * the n x n state does not fit, and the device-side errors above.
+ */
+int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src,
+                   const int32_t* dst, const int64_t* w, uint32_t flags, void* cuda_stream);
+
+/*
+ * bc_apply_edge_update -- one incremental edge update (u, v, w_new): a new edge, or a
+ * lower weight of an existing one (Section 3, Algorithm 3 with Lemma 2; undirected
+ * graphs as the two arcs of G_D).  Synchronous.
+ *   Rejects u or v out of range, u == v, w_new < 1 or >= INF (BC_ERR_ARG) and
+ *   w_new >= current weight (BC_ERR_NOT_INCREMENTAL), leaving the state untouched.
+ */
+int bc_apply_edge_update(bc_graph* g, int32_t u, int32_t v, int64_t w_new);
+
+/*
+ * bc_apply_vertex_update -- one incremental vertex update of v over k incident edges
+ * (Section 4: E_i processed first with Algorithm 4 and Lemma 4, then E_o on the
+ * reversed graph).  nbr, w_new and dir are host arrays of k entries; dir[i] == 0
+ * is the edge (nbr[i], v), 1 is (v, nbr[i]); dir may be NULL for an undirected
+ * graph (where it is ignored).  Synchronous.  Rejects an empty or repeated edge set
+ * and each edge as bc_apply_edge_update would, leaving the state untouched.
+ */
+int bc_apply_vertex_update(bc_graph* g, int32_t v, int32_t k, const int32_t* nbr,
+                           const int64_t* w_new, const uint8_t* dir);
+
+/*
+ * bc_apply_updates -- apply count updates in order, each seeing the state left by
+ * the one before (bc_stage_updates + bc_run_staged + bc_synchronize).
+ *   ups     host array of count bc_update records.
+ *   edges   host array holding every vertex update's edges (may be NULL if none).
+ *   n_edges number of entries in edges.
+ *   n_done  (optional) receives how many updates were enqueued before the first
+ *           rejected one (count when all were valid).
+ * Stops at the first invalid update and returns its status; the updates before it
+ * are applied.
+ */
+int bc_apply_updates(bc_graph* g, int32_t count, const bc_update* ups,
+                     const bc_vedge* edges, int64_t n_edges, int32_t* n_done);
+
+/*
+ * bc_stage_updates -- copy a batch to the handle: the records to host memory owned by
+ * the handle and the vertex-update edges to device memory.  Nothing is validated or
+ * run yet.  Replaces any batch staged before.  Synchronous (the copy completes).
+ */
+int bc_stage_updates(bc_graph* g, int32_t count, const bc_update* ups,
+                     const bc_vedge* edges, int64_t n_edges);
+
+/*
+ * bc_run_staged -- validate the staged updates in order and enqueue the device work of
+ * each valid one on the handle's stream.  Does not wait for the device; call
+ * bc_synchronize for device-side errors.  Stops at the first invalid update and
+ * returns its status (n_done as in bc_apply_updates).
+ */
+int bc_run_staged(bc_graph* g, int32_t* n_done);
+
+/* bc_synchronize -- wait for the handle's stream and return any device-side error. */
+int bc_synchronize(bc_graph* g);
+
+/*
+ * bc_query -- non-blocking: BC_OK with *done = 1 when every enqueued update has
+ * finished on the device (device-side errors are then reported as by
+ * bc_synchronize), *done = 0 while work is still in flight.
+ */
+int bc_query(bc_graph* g, int32_t* done);
+
+/*
+ * bc_get_scores -- BC(v) for every v (Eq. 3), into the host array out[n].
+ * Synchronous.  Undirected graphs: halved G_D sums.
+ */
+int bc_get_scores(bc_graph* g, double* out);
+
+/*
+ * bc_get_rows -- copy rows s0 .. s0+count-1 of the state to host arrays of count*n
+ * entries each (any of them may be NULL): d widened to int64 (INF -> INT64_MAX),
+ * sigma, and delta_s.(t) (0 on the diagonal and for unreachable t).  Synchronous.
+ */
+int bc_get_rows(bc_graph* g, int32_t s0, int32_t count, int64_t* d_out,
+                uint64_t* sigma_out, double* delta_out);
+
+/* bc_get_info -- counters of the handle (synchronous). */
+int bc_get_info(bc_graph* g, bc_info* out);
+
+/*
+ * bc_set_option -- tuning knobs (documented values only):
+ *   "full_scan" 0|1: run the rank-1 pass of Lemma 2 / 4 over every row instead of
+ *                     only the rows that can change (Section 5 scans all n^2 pairs).
+ */
+int bc_set_option(bc_graph* g, const char* name, int64_t value);
+
+/* bc_destroy -- free the handle and its device memory (waits for its stream). */
+void bc_destroy(bc_graph* g);
+
+/* bc_last_error -- text of the last error of the handle ("" if none); valid until
+ * the next call on the handle.  g may be NULL for errors of a failed bc_init_static. */
+const char* bc_last_error(const bc_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCGPU_H */

@@ -1,0 +1,220 @@
+"""ctypes binding of libbcgpu.so (declared in include/bcgpu.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA library.
+The module-level functions carry the C names; ``BCGraph`` wraps a handle.  Loading
+fails loudly when the library has not been built (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BC_OK = 0
+BC_ERR_ARG = -1
+BC_ERR_NOT_INCREMENTAL = -2
+BC_ERR_OVERFLOW = -3
+BC_ERR_DIST_OVERFLOW = -4
+BC_ERR_OOM = -5
+BC_ERR_CUDA = -6
+BC_ERR_TIMEOUT = -7
+BC_ERR_POISONED = -8
+
+BC_DIRECTED = 1
+BC_UNDIRECTED = 2
+BC_DIST_I32 = 16
+BC_DIST_I64 = 32
+BC_UPD_EDGE = 0
+BC_UPD_VERTEX = 1
+
+UPDATE_DTYPE = np.dtype([("kind", "<i4"), ("u", "<i4"), ("v", "<i4"), ("k", "<i4"),
+                         ("w", "<i8"), ("first", "<i8")], align=True)
+VEDGE_DTYPE = np.dtype([("x", "<i4"), ("dir", "<i4"), ("w", "<i8")], align=True)
+assert UPDATE_DTYPE.itemsize == 32 and VEDGE_DTYPE.itemsize == 16
+
+INF64 = np.iinfo(np.int64).max
+
+EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "bc_apply_updates",
+           "bc_stage_updates", "bc_run_staged", "bc_synchronize", "bc_query", "bc_get_scores",
+           "bc_get_rows", "bc_get_info", "bc_set_option", "bc_destroy", "bc_last_error"]
+
+
+class bc_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("directed", ctypes.c_int32), ("dist_bytes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("m", ctypes.c_int64), ("estar_arcs", ctypes.c_int64),
+                ("updates_applied", ctypes.c_int64), ("rows_reaccumulated", ctypes.c_int64),
+                ("noop_updates", ctypes.c_int64), ("max_rows", ctypes.c_int64),
+                ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double)]
+
+
+class BCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bcgpu error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbcgpu.so (building it first when asked); raises when it cannot be had."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbcgpu.so is not built ({path}); run paper_1311_2147_gb300.build")
+    lib = ctypes.CDLL(path)
+    p, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "bc_init_static": ([ctypes.POINTER(p), i32, i64, p, p, p, u32, p], ctypes.c_int),
+        "bc_apply_edge_update": ([p, i32, i32, i64], ctypes.c_int),
+        "bc_apply_vertex_update": ([p, i32, i32, p, p, p], ctypes.c_int),
+        "bc_apply_updates": ([p, i32, p, p, i64, ctypes.POINTER(i32)], ctypes.c_int),
+        "bc_stage_updates": ([p, i32, p, p, i64], ctypes.c_int),
+        "bc_run_staged": ([p, ctypes.POINTER(i32)], ctypes.c_int),
+        "bc_synchronize": ([p], ctypes.c_int),
+        "bc_query": ([p, ctypes.POINTER(i32)], ctypes.c_int),
+        "bc_get_scores": ([p, p], ctypes.c_int),
+        "bc_get_rows": ([p, i32, i32, p, p, p], ctypes.c_int),
+        "bc_get_info": ([p, ctypes.POINTER(bc_info)], ctypes.c_int),
+        "bc_set_option": ([p, ctypes.c_char_p, i64], ctypes.c_int),
+        "bc_destroy": ([p], None),
+        "bc_last_error": ([p], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def encode_updates(ups):
+    """Turn ("edge", u, v, w) / ("vertex", v, [(x, w, dir), ...]) tuples into the
+    bc_update / bc_vedge arrays of the ABI."""
+    rec = np.zeros(len(ups), dtype=UPDATE_DTYPE)
+    edges = []
+    for i, up in enumerate(ups):
+        if up[0] == "edge":
+            _, u, v, w = up
+            rec[i] = (BC_UPD_EDGE, u, v, 0, w, 0)
+        else:
+            _, v, es = up
+            rec[i] = (BC_UPD_VERTEX, -1, v, len(es), 0, len(edges))
+            for x, w, d in es:
+                edges.append((x, d, w))
+    ed = np.array(edges, dtype=VEDGE_DTYPE) if edges else np.zeros(0, dtype=VEDGE_DTYPE)
+    return rec, ed
+
+
+class BCGraph:
+    """One device-resident graph state."""
+
+    def __init__(self, g, dist: str = "i32", stream=None):
+        lib = load()
+        self.lib = lib
+        self.n = int(g.n)
+        self.directed = bool(g.directed)
+        src = np.ascontiguousarray(g.src, dtype=np.int32)
+        dst = np.ascontiguousarray(g.dst, dtype=np.int32)
+        w = np.ascontiguousarray(g.w, dtype=np.int64)
+        flags = (BC_DIRECTED if self.directed else BC_UNDIRECTED) | (BC_DIST_I32 if dist == "i32" else BC_DIST_I64)
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = lib.bc_init_static(ctypes.byref(h), self.n, int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(w),
+                                flags, st)
+        if rc != BC_OK:
+            raise BCError(rc, lib.bc_last_error(None).decode())
+        self.h = h
+
+    # -- errors
+    def _check(self, rc):
+        if rc != BC_OK:
+            raise BCError(rc, self.lib.bc_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- updates
+    def bc_apply_edge_update(self, u, v, w):
+        return self.lib.bc_apply_edge_update(self.h, int(u), int(v), int(w))
+
+    def bc_apply_vertex_update(self, v, nbr, w, dirs=None):
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int64)
+        d = None if dirs is None else np.ascontiguousarray(dirs, dtype=np.uint8)
+        return self.lib.bc_apply_vertex_update(self.h, int(v), int(nbr.shape[0]), _ptr(nbr), _ptr(w), _ptr(d))
+
+    def bc_apply_updates(self, ups):
+        rec, ed = encode_updates(ups) if isinstance(ups, list) else ups
+        done = ctypes.c_int32(0)
+        rc = self.lib.bc_apply_updates(self.h, int(rec.shape[0]), _ptr(rec), _ptr(ed) if ed.size else None,
+                                       int(ed.shape[0]), ctypes.byref(done))
+        return rc, done.value
+
+    def bc_stage_updates(self, ups):
+        rec, ed = encode_updates(ups) if isinstance(ups, list) else ups
+        self._staged = (rec, ed)
+        return self.lib.bc_stage_updates(self.h, int(rec.shape[0]), _ptr(rec), _ptr(ed) if ed.size else None,
+                                         int(ed.shape[0]))
+
+    def bc_run_staged(self):
+        done = ctypes.c_int32(0)
+        rc = self.lib.bc_run_staged(self.h, ctypes.byref(done))
+        return rc, done.value
+
+    def bc_synchronize(self):
+        return self.lib.bc_synchronize(self.h)
+
+    def bc_query(self):
+        done = ctypes.c_int32(0)
+        rc = self.lib.bc_query(self.h, ctypes.byref(done))
+        return rc, bool(done.value)
+
+    def bc_set_option(self, name: str, value: int):
+        return self._check(self.lib.bc_set_option(self.h, name.encode(), int(value)))
+
+    # -- results
+    def bc_get_scores(self):
+        out = np.empty(self.n, dtype=np.float64)
+        self._check(self.lib.bc_get_scores(self.h, _ptr(out)))
+        return out
+
+    def bc_get_rows(self, s0=0, count=None, want=("d", "sigma", "delta")):
+        count = self.n - s0 if count is None else count
+        d = np.empty((count, self.n), np.int64) if "d" in want else None
+        s = np.empty((count, self.n), np.uint64) if "sigma" in want else None
+        dl = np.empty((count, self.n), np.float64) if "delta" in want else None
+        self._check(self.lib.bc_get_rows(self.h, int(s0), int(count), _ptr(d), _ptr(s), _ptr(dl)))
+        return d, s, dl
+
+    def bc_get_info(self):
+        info = bc_info()
+        self._check(self.lib.bc_get_info(self.h, ctypes.byref(info)))
+        return {k: getattr(info, k) for k, _ in bc_info._fields_}
+
+    def last_error(self):
+        return self.lib.bc_last_error(self.h).decode()

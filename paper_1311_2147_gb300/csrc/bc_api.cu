@@ -1,0 +1,745 @@
+// bc_api.cu -- host side of libbcgpu.so: handles, validation, the E* superset and the
+// launch sequence of every update.  Declarations and conventions: include/bcgpu.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "bcgpu.h"
+#include "bc_internal.cuh"
+
+using namespace bcg;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+inline uint64_t arc_key(int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
+
+struct Arc {
+    int32_t a, b;
+    int64_t w;
+};
+
+}  // namespace
+
+struct bc_graph {
+    Dev d{};
+    int32_t n = 0;
+    bool directed = true;
+    int dbytes = 4;
+    int64_t inf = INT32_MAX;
+    bool poisoned = false;
+    int poison_status = BC_OK;
+    std::string last_error;
+    bool full_scan = false;
+    // weights of every arc of G (G_D for undirected graphs)
+    std::unordered_map<uint64_t, int64_t> wmap;
+    // host mirror of the E* superset CSR
+    std::vector<int32_t> e_off, e_len, e_src, e_dst;
+    std::vector<int64_t> e_w;
+    std::unordered_map<uint64_t, int32_t> eslot;
+    int64_t estar_arcs = 0;
+    // staged batch
+    std::vector<bc_update> staged;
+    std::vector<int64_t> staged_first;   // first device entry of each staged update
+    std::vector<int32_t> staged_k;
+    std::vector<VEdge> h_entries;
+    VEdge* d_entries = nullptr;
+    int64_t d_entries_cap = 0;
+    // bookkeeping
+    int32_t* h_err = nullptr;             // pinned
+    int64_t* h_stats = nullptr;           // pinned
+    uint8_t* d_keep = nullptr;
+    int64_t d_keep_cap = 0;
+    cudaEvent_t ev_done = nullptr;
+    int64_t bytes = 0;
+    double last_init_ms = 0.0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(bc_graph* g, int code, const std::string& msg) {
+    if (g) g->last_error = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(bc_graph* g, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(g, BC_ERR_OOM, m);
+    return fail(g, BC_ERR_CUDA, m);
+}
+
+#define CK(g, call)                                               \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, #call);  \
+    } while (0)
+
+template <typename T>
+int dalloc(bc_graph* g, T** p, size_t count) {
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc");
+    g->allocs.push_back(*p);
+    g->bytes += (int64_t)bytes;
+    return BC_OK;
+}
+
+void dfree(bc_graph* g, void* p) {
+    if (!p) return;
+    auto it = std::find(g->allocs.begin(), g->allocs.end(), p);
+    if (it != g->allocs.end()) g->allocs.erase(it);
+    cudaFree(p);
+}
+
+int status_of_err(int32_t f) {
+    if (f & ERRF_OVERFLOW) return BC_ERR_OVERFLOW;
+    if (f & ERRF_DIST) return BC_ERR_DIST_OVERFLOW;
+    if (f & ERRF_TIMEOUT) return BC_ERR_TIMEOUT;
+    return BC_OK;
+}
+
+const char* status_text(int s) {
+    switch (s) {
+        case BC_ERR_OVERFLOW: return "a shortest-path count does not fit in 64 bits";
+        case BC_ERR_DIST_OVERFLOW: return "a distance does not fit the distance type";
+        case BC_ERR_TIMEOUT: return "a bounded device wait gave up";
+        default: return "";
+    }
+}
+
+// Wait for the stream and turn a device-side error into a status (poisoning the handle).
+int sync_check(bc_graph* g) {
+    CK(g, cudaStreamSynchronize(g->d.st));
+    CK(g, cudaMemcpy(g->h_err, g->d.err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (*g->h_err) {
+        g->poisoned = true;
+        g->poison_status = status_of_err(*g->h_err);
+        return fail(g, g->poison_status, status_text(g->poison_status));
+    }
+    return BC_OK;
+}
+
+// Lay the E* superset out with slack per vertex and upload it.
+int estar_layout(bc_graph* g, const std::vector<Arc>& arcs) {
+    const int32_t n = g->n;
+    std::vector<int32_t> deg(n, 0);
+    for (const Arc& x : arcs) deg[x.a]++;
+    g->e_off.assign(n + 1, 0);
+    g->e_len.assign(n, 0);
+    for (int32_t a = 0; a < n; ++a) g->e_off[a + 1] = g->e_off[a] + deg[a] + 2 + deg[a] / 8;
+    const int64_t cap = g->e_off[n];
+    g->e_src.assign(cap, 0);
+    g->e_dst.assign(cap, -1);
+    g->e_w.assign(cap, 0);
+    g->eslot.clear();
+    g->eslot.reserve(arcs.size() * 2 + 16);
+    for (const Arc& x : arcs) {
+        const int32_t slot = g->e_off[x.a] + g->e_len[x.a]++;
+        g->e_src[slot] = x.a;
+        g->e_dst[slot] = x.b;
+        g->e_w[slot] = x.w;
+        g->eslot[arc_key(x.a, x.b)] = slot;
+    }
+    for (int32_t a = 0; a < n; ++a)
+        for (int32_t s = g->e_off[a]; s < g->e_off[a + 1]; ++s) g->e_src[s] = a;
+    g->estar_arcs = (int64_t)arcs.size();
+    Dev& d = g->d;
+    if (cap > d.e_cap) {
+        dfree(g, d.e_src);
+        dfree(g, d.e_dst);
+        dfree(g, d.e_w);
+        d.e_src = d.e_dst = nullptr;
+        d.e_w = nullptr;
+        const int64_t ncap = cap + cap / 4 + 64;
+        int rc;
+        if ((rc = dalloc(g, &d.e_src, ncap)) || (rc = dalloc(g, &d.e_dst, ncap))) return rc;
+        if (g->dbytes == 4) {
+            int32_t* p;
+            if ((rc = dalloc(g, &p, ncap))) return rc;
+            d.e_w = p;
+        } else {
+            int64_t* p;
+            if ((rc = dalloc(g, &p, ncap))) return rc;
+            d.e_w = p;
+        }
+        d.e_cap = ncap;
+    }
+    // free slots beyond the layout stay empty (dst = -1)
+    std::vector<int32_t> dst_full(d.e_cap, -1), src_full(d.e_cap, 0);
+    std::copy(g->e_dst.begin(), g->e_dst.end(), dst_full.begin());
+    std::copy(g->e_src.begin(), g->e_src.end(), src_full.begin());
+    CK(g, cudaMemcpyAsync(d.e_off, g->e_off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, d.st));
+    CK(g, cudaMemcpyAsync(d.e_len, g->e_len.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, d.st));
+    CK(g, cudaMemcpyAsync(d.e_src, src_full.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
+    CK(g, cudaMemcpyAsync(d.e_dst, dst_full.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
+    if (g->dbytes == 4) {
+        std::vector<int32_t> w32(d.e_cap, 0);
+        for (int64_t i = 0; i < cap; ++i) w32[i] = (int32_t)g->e_w[i];
+        CK(g, cudaMemcpyAsync(d.e_w, w32.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
+        CK(g, cudaStreamSynchronize(d.st));
+    } else {
+        std::vector<int64_t> w64(d.e_cap, 0);
+        std::copy(g->e_w.begin(), g->e_w.end(), w64.begin());
+        CK(g, cudaMemcpyAsync(d.e_w, w64.data(), sizeof(int64_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
+        CK(g, cudaStreamSynchronize(d.st));
+    }
+    return BC_OK;
+}
+
+// Rebuild the E* superset when a vertex runs out of slack: keep the arcs that are still
+// in E* (w = d), add the pending arcs, lay out again.
+int estar_rebuild(bc_graph* g, const std::vector<Arc>& pending) {
+    int rc = sync_check(g);
+    if (rc) return rc;
+    Dev& d = g->d;
+    if (d.e_cap > g->d_keep_cap) {
+        dfree(g, g->d_keep);
+        g->d_keep = nullptr;
+        if ((rc = dalloc(g, &g->d_keep, d.e_cap))) return rc;
+        g->d_keep_cap = d.e_cap;
+    }
+    launch_estar_keep(d, g->d_keep);
+    std::vector<uint8_t> keep(d.e_cap);
+    CK(g, cudaMemcpyAsync(keep.data(), g->d_keep, d.e_cap, cudaMemcpyDeviceToHost, d.st));
+    CK(g, cudaStreamSynchronize(d.st));
+    std::unordered_set<uint64_t> pend;
+    for (const Arc& x : pending) pend.insert(arc_key(x.a, x.b));
+    std::vector<Arc> arcs;
+    arcs.reserve(g->estar_arcs + pending.size());
+    const int64_t cap = (int64_t)g->e_dst.size();
+    for (int64_t s = 0; s < cap; ++s) {
+        if (g->e_dst[s] < 0 || !keep[s]) continue;
+        if (pend.count(arc_key(g->e_src[s], g->e_dst[s]))) continue;
+        arcs.push_back({g->e_src[s], g->e_dst[s], g->e_w[s]});
+    }
+    for (const Arc& x : pending) arcs.push_back(x);
+    return estar_layout(g, arcs);
+}
+
+// Validate one update against the host weights and produce its edge entries (at vertex
+// v).  Does not modify anything.
+int validate_update(bc_graph* g, const bc_update& u, const bc_vedge* edges, int64_t n_edges,
+                    int32_t* v_out, std::vector<VEdge>& ent) {
+    ent.clear();
+    const int32_t n = g->n;
+    auto check_arc = [&](int32_t a, int32_t b, int64_t w) -> int {
+        if (a < 0 || a >= n || b < 0 || b >= n || a == b)
+            return fail(g, BC_ERR_ARG, "edge endpoint out of range or self-loop");
+        if (w < 1 || w >= g->inf) return fail(g, BC_ERR_ARG, "weight outside [1, INF-1]");
+        auto it = g->wmap.find(arc_key(a, b));
+        if (it != g->wmap.end() && w >= it->second)
+            return fail(g, BC_ERR_NOT_INCREMENTAL, "new weight is not below the current weight");
+        return BC_OK;
+    };
+    if (u.kind == BC_UPD_EDGE) {
+        int rc = check_arc(u.u, u.v, u.w);
+        if (rc) return rc;
+        *v_out = u.v;
+        ent.push_back({u.u, 0, u.w});
+        return BC_OK;
+    }
+    if (u.kind != BC_UPD_VERTEX) return fail(g, BC_ERR_ARG, "unknown update kind");
+    if (u.v < 0 || u.v >= n) return fail(g, BC_ERR_ARG, "vertex out of range");
+    if (u.k < 1) return fail(g, BC_ERR_ARG, "empty vertex update");
+    if (!edges || u.first < 0 || u.first + u.k > n_edges) return fail(g, BC_ERR_ARG, "vertex update edges out of range");
+    std::unordered_set<uint64_t> seen;
+    for (int32_t j = 0; j < u.k; ++j) {
+        const bc_vedge& e = edges[u.first + j];
+        int32_t dir = g->directed ? e.dir : 0;
+        if (g->directed && dir != 0 && dir != 1) return fail(g, BC_ERR_ARG, "edge direction must be 0 or 1");
+        if (!seen.insert(arc_key(e.x, dir)).second) return fail(g, BC_ERR_ARG, "repeated edge in a vertex update");
+        int rc = (dir == 0) ? check_arc(e.x, u.v, e.w) : check_arc(u.v, e.x, e.w);
+        if (rc) return rc;
+        ent.push_back({e.x, dir, e.w});
+    }
+    *v_out = u.v;
+    return BC_OK;
+}
+
+// Apply a validated update to the host weights and the E* superset mirror; fills the
+// device writes to make.  Sets *rebuild when a vertex has no free slot left.
+void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::vector<EOp>& ops,
+                   std::vector<Arc>& arcs, bool* rebuild) {
+    arcs.clear();
+    for (const VEdge& e : ent) {
+        if (!g->directed) {
+            arcs.push_back({e.x, v, e.w});
+            arcs.push_back({v, e.x, e.w});
+        } else if (e.dir == 0) {
+            arcs.push_back({e.x, v, e.w});
+        } else {
+            arcs.push_back({v, e.x, e.w});
+        }
+    }
+    *rebuild = false;
+    ops.clear();
+    for (const Arc& x : arcs) {
+        g->wmap[arc_key(x.a, x.b)] = x.w;
+        auto it = g->eslot.find(arc_key(x.a, x.b));
+        if (it != g->eslot.end()) {
+            g->e_w[it->second] = x.w;
+            ops.push_back({it->second, x.a, x.b, g->e_len[x.a], x.w});
+            continue;
+        }
+        const int32_t a = x.a;
+        if (g->e_off[a] + g->e_len[a] >= g->e_off[a + 1]) {
+            *rebuild = true;
+            continue;
+        }
+        const int32_t slot = g->e_off[a] + g->e_len[a]++;
+        g->e_src[slot] = a;
+        g->e_dst[slot] = x.b;
+        g->e_w[slot] = x.w;
+        g->eslot[arc_key(a, x.b)] = slot;
+        g->estar_arcs++;
+        ops.push_back({slot, a, x.b, g->e_len[a], x.w});
+    }
+}
+
+int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const VEdge* d_ent) {
+    Dev& d = g->d;
+    std::vector<EOp> ops;
+    std::vector<Arc> arcs;
+    bool rebuild = false;
+    mirror_update(g, v, ent, ops, arcs, &rebuild);
+    if (rebuild) {
+        int rc = estar_rebuild(g, arcs);
+        if (rc) return rc;
+    } else {
+        for (size_t i = 0; i < ops.size(); i += kMaxEOps) {
+            EOps pack{};
+            pack.count = (int32_t)std::min<size_t>(kMaxEOps, ops.size() - i);
+            for (int j = 0; j < pack.count; ++j) pack.op[j] = ops[i + j];
+            launch_estar_write(d, pack);
+        }
+    }
+    int32_t kin = 0, kout = 0;
+    for (const VEdge& e : ent) {
+        if (!g->directed || e.dir == 0) kin++;
+        if (!g->directed || e.dir == 1) kout++;
+    }
+    const int32_t k = (int32_t)ent.size();
+    const int full = g->full_scan ? 1 : 0;
+    if (kin) {
+        launch_alg4_in(d, v, d_ent, k);
+        launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0);
+        launch_scan_in(d, v);
+    }
+    if (kout) {
+        launch_alg4_out(d, v, d_ent, k);
+        launch_rows_out(d, v, d_ent, k);
+        launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0);
+        launch_scan_out(d, v);
+        launch_write_row(d, v);
+    }
+    launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1);
+    launch_bc_rows(d, -1, 0);
+    launch_accum(d, 0);
+    launch_bc_rows(d, +1, 0);
+    CK(g, cudaGetLastError());
+    return BC_OK;
+}
+
+void destroy_all(bc_graph* g) {
+    if (!g) return;
+    if (g->d.st || true) cudaStreamSynchronize(g->d.st);
+    for (void* p : g->allocs) cudaFree(p);
+    g->allocs.clear();
+    if (g->h_err) cudaFreeHost(g->h_err);
+    if (g->h_stats) cudaFreeHost(g->h_stats);
+    if (g->ev_done) cudaEventDestroy(g->ev_done);
+    delete g;
+}
+
+bool check_alive(bc_graph* g, int* rc) {
+    if (!g) {
+        *rc = BC_ERR_ARG;
+        return false;
+    }
+    if (g->poisoned) {
+        g->last_error = "handle poisoned by an earlier device-side error";
+        *rc = BC_ERR_POISONED;
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                   const int64_t* w, uint32_t flags, void* cuda_stream) {
+    if (!out) return fail(nullptr, BC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const bool dir = (flags & BC_DIRECTED) != 0, und = (flags & BC_UNDIRECTED) != 0;
+    const bool i32 = (flags & BC_DIST_I32) != 0, i64 = (flags & BC_DIST_I64) != 0;
+    if (dir == und || i32 == i64) return fail(nullptr, BC_ERR_ARG, "flags need one of DIRECTED/UNDIRECTED and one of DIST_I32/DIST_I64");
+    if (n < 1 || n > 65536) return fail(nullptr, BC_ERR_ARG, "n must be in [1, 65536]");
+    if (m < 0 || (m > 0 && (!src || !dst || !w))) return fail(nullptr, BC_ERR_ARG, "bad edge arrays");
+    bc_graph* g = new bc_graph();
+    g->n = n;
+    g->directed = dir;
+    g->dbytes = i32 ? 4 : 8;
+    g->inf = i32 ? (int64_t)INT32_MAX : INT64_MAX;
+    Dev& d = g->d;
+    d.n = n;
+    d.dbytes = g->dbytes;
+    d.directed = dir ? 1 : 0;
+    d.st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) {
+        int rc = cuda_fail(nullptr, ce, "cudaGetDevice");
+        delete g;
+        return rc;
+    }
+    // ---- arcs of G (G_D), validated
+    const int64_t arcs = dir ? m : 2 * m;
+    std::vector<Arc> all;
+    all.reserve(arcs);
+    g->wmap.reserve(arcs * 2 + 16);
+    for (int64_t i = 0; i < m; ++i) {
+        const int32_t a = src[i], b = dst[i];
+        if (a < 0 || a >= n || b < 0 || b >= n || a == b || w[i] < 1 || w[i] >= g->inf) {
+            destroy_all(g);
+            return fail(nullptr, BC_ERR_ARG, "edge out of range, self-loop or weight outside [1, INF-1]");
+        }
+        if (!g->wmap.emplace(arc_key(a, b), w[i]).second || (!dir && !g->wmap.emplace(arc_key(b, a), w[i]).second)) {
+            destroy_all(g);
+            return fail(nullptr, BC_ERR_ARG, "repeated edge");
+        }
+        all.push_back({a, b, w[i]});
+        if (!dir) all.push_back({b, a, w[i]});
+    }
+    // CSR of G by tail
+    std::vector<int32_t> off(n + 1, 0), csrc(arcs), cdst(arcs);
+    std::vector<int64_t> cw(arcs);
+    for (const Arc& x : all) off[x.a + 1]++;
+    for (int32_t a = 0; a < n; ++a) off[a + 1] += off[a];
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (const Arc& x : all) {
+            const int32_t p = pos[x.a]++;
+            csrc[p] = x.a;
+            cdst[p] = x.b;
+            cw[p] = x.w;
+        }
+    }
+    // ---- device memory
+    const size_t nn = (size_t)n * n;
+    int rc = BC_OK;
+    d.acc_grid = d.nsm * 2;
+    d.ws_stride = ((3 * (int64_t)n + 2) + 3) & ~(int64_t)3;
+    d.nrb_max = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+    d.g_arcs = arcs;
+    if (g->dbytes == 4) {
+        int32_t *pD, *pfD, *pcD, *pgw;
+        if ((rc = dalloc(g, &pD, nn)) || (rc = dalloc(g, &pfD, n)) || (rc = dalloc(g, &pcD, n)) ||
+            (rc = dalloc(g, &pgw, arcs))) {
+            destroy_all(g);
+            return fail(nullptr, rc, "device allocation failed");
+        }
+        d.D = pD; d.fD = pfD; d.cD = pcD; d.g_w = pgw;
+    } else {
+        int64_t *pD, *pfD, *pcD, *pgw;
+        if ((rc = dalloc(g, &pD, nn)) || (rc = dalloc(g, &pfD, n)) || (rc = dalloc(g, &pcD, n)) ||
+            (rc = dalloc(g, &pgw, arcs))) {
+            destroy_all(g);
+            return fail(nullptr, rc, "device allocation failed");
+        }
+        d.D = pD; d.fD = pfD; d.cD = pcD; d.g_w = pgw;
+    }
+    if ((rc = dalloc(g, &d.S, nn)) || (rc = dalloc(g, &d.Dl, nn)) || (rc = dalloc(g, &d.bc_hi, n)) ||
+        (rc = dalloc(g, &d.bc_lo, n)) || (rc = dalloc(g, &d.g_off, n + 1)) || (rc = dalloc(g, &d.g_src, arcs)) ||
+        (rc = dalloc(g, &d.g_dst, arcs)) || (rc = dalloc(g, &d.e_off, n + 1)) || (rc = dalloc(g, &d.e_len, n)) ||
+        (rc = dalloc(g, &d.err, 1)) || (rc = dalloc(g, &d.stats, 8)) || (rc = dalloc(g, &d.mark, n)) ||
+        (rc = dalloc(g, &d.changed, n)) || (rc = dalloc(g, &d.rows, n)) || (rc = dalloc(g, &d.acc_rows, n)) ||
+        (rc = dalloc(g, &d.counts, 4)) || (rc = dalloc(g, &d.fS, n)) || (rc = dalloc(g, &d.fM, n)) ||
+        (rc = dalloc(g, &d.cS, n)) || (rc = dalloc(g, &d.cM, n)) ||
+        (rc = dalloc(g, &d.partial, (size_t)d.nrb_max * n)) ||
+        (rc = dalloc(g, &d.ws, (size_t)d.acc_grid * d.ws_stride))) {
+        destroy_all(g);
+        return fail(nullptr, rc, "device allocation failed");
+    }
+    if (cudaMallocHost(&g->h_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&g->h_stats, 8 * sizeof(int64_t)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+        destroy_all(g);
+        return fail(nullptr, BC_ERR_OOM, "pinned host allocation failed");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto bail = [&](int code, const std::string& msg) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        destroy_all(g);
+        return fail(nullptr, code, msg);
+    };
+#define CKI(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bail(e_ == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+    CKI(cudaMemsetAsync(d.err, 0, sizeof(int32_t), d.st));
+    CKI(cudaMemsetAsync(d.stats, 0, 8 * sizeof(int64_t), d.st));
+    CKI(cudaMemsetAsync(d.mark, 0, n, d.st));
+    CKI(cudaMemsetAsync(d.changed, 0, n, d.st));
+    CKI(cudaMemsetAsync(d.counts, 0, 4 * sizeof(int32_t), d.st));
+    CKI(cudaStreamSynchronize(d.st));
+    CKI(cudaEventRecord(e0, d.st));
+    CKI(cudaMemcpyAsync(d.g_off, off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, d.st));
+    CKI(cudaMemcpyAsync(d.g_src, csrc.data(), sizeof(int32_t) * arcs, cudaMemcpyHostToDevice, d.st));
+    CKI(cudaMemcpyAsync(d.g_dst, cdst.data(), sizeof(int32_t) * arcs, cudaMemcpyHostToDevice, d.st));
+    std::vector<int32_t> w32;
+    if (g->dbytes == 4) {
+        w32.resize(arcs);
+        for (int64_t i = 0; i < arcs; ++i) w32[i] = (int32_t)cw[i];
+        CKI(cudaMemcpyAsync(d.g_w, w32.data(), sizeof(int32_t) * arcs, cudaMemcpyHostToDevice, d.st));
+    } else {
+        CKI(cudaMemcpyAsync(d.g_w, cw.data(), sizeof(int64_t) * arcs, cudaMemcpyHostToDevice, d.st));
+    }
+    // all-pairs distances, then E* read off them
+    launch_sssp(d);
+    uint8_t* d_flags = nullptr;
+    if ((rc = dalloc(g, &d_flags, arcs))) return bail(rc, "device allocation failed");
+    launch_estar_flags(d, d_flags);
+    std::vector<uint8_t> eflags(arcs);
+    CKI(cudaMemcpyAsync(eflags.data(), d_flags, arcs, cudaMemcpyDeviceToHost, d.st));
+    CKI(cudaStreamSynchronize(d.st));
+    CKI(cudaGetLastError());
+    dfree(g, d_flags);
+    g->bytes -= (int64_t)std::max<int64_t>(arcs, 1);
+    {
+        std::vector<Arc> estar;
+        for (int64_t i = 0; i < arcs; ++i)
+            if (eflags[i]) estar.push_back({csrc[i], cdst[i], cw[i]});
+        if ((rc = estar_layout(g, estar))) return bail(rc, g->last_error);
+    }
+    // path counts, DAGs and dependencies of every source; BC as column sums
+    launch_accum(d, 1);
+    launch_bc_rows(d, +1, 1);
+    CKI(cudaGetLastError());
+    CKI(cudaEventRecord(e1, d.st));
+    CKI(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    g->last_init_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+#undef CKI
+    rc = sync_check(g);
+    if (rc) {
+        std::string msg = g->last_error;
+        destroy_all(g);
+        return fail(nullptr, rc, msg);
+    }
+    *out = g;
+    return BC_OK;
+}
+
+int bc_stage_updates(bc_graph* g, int32_t count, const bc_update* ups, const bc_vedge* edges,
+                     int64_t n_edges) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (count < 0 || (count > 0 && !ups) || n_edges < 0 || (n_edges > 0 && !edges))
+        return fail(g, BC_ERR_ARG, "bad batch arrays");
+    g->staged.assign(ups, ups + count);
+    g->staged_first.assign(count, 0);
+    g->staged_k.assign(count, 0);
+    g->h_entries.clear();
+    for (int32_t i = 0; i < count; ++i) {
+        const bc_update& u = ups[i];
+        g->staged_first[i] = (int64_t)g->h_entries.size();
+        if (u.kind == BC_UPD_EDGE) {
+            g->h_entries.push_back({u.u, 0, u.w});
+            g->staged_k[i] = 1;
+        } else if (u.kind == BC_UPD_VERTEX && u.k > 0 && u.first >= 0 && u.first + u.k <= n_edges) {
+            for (int32_t j = 0; j < u.k; ++j) {
+                const bc_vedge& e = edges[u.first + j];
+                g->h_entries.push_back({e.x, g->directed ? e.dir : 0, e.w});
+            }
+            g->staged_k[i] = u.k;
+        }
+    }
+    const int64_t need = (int64_t)g->h_entries.size();
+    if (need > g->d_entries_cap) {
+        CK(g, cudaStreamSynchronize(g->d.st));
+        dfree(g, g->d_entries);
+        g->d_entries = nullptr;
+        const int64_t cap = std::max<int64_t>(need, 1024);
+        if ((rc = dalloc(g, &g->d_entries, cap))) return rc;
+        g->d_entries_cap = cap;
+    }
+    if (need > 0) {
+        CK(g, cudaMemcpyAsync(g->d_entries, g->h_entries.data(), sizeof(VEdge) * need,
+                              cudaMemcpyHostToDevice, g->d.st));
+        CK(g, cudaStreamSynchronize(g->d.st));
+    }
+    // keep the caller's edges for validation in bc_run_staged
+    g->h_entries.shrink_to_fit();
+    return BC_OK;
+}
+
+int bc_run_staged(bc_graph* g, int32_t* n_done) {
+    int rc;
+    if (n_done) *n_done = 0;
+    if (!check_alive(g, &rc)) return rc;
+    std::vector<VEdge> ent;
+    std::vector<bc_vedge> tmp;
+    const int32_t count = (int32_t)g->staged.size();
+    int32_t done = 0;
+    rc = BC_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        const bc_update& u = g->staged[i];
+        // validation reads the staged entries (already in bc_vedge form)
+        tmp.clear();
+        bc_update uu = u;
+        if (u.kind == BC_UPD_VERTEX) {
+            if (g->staged_k[i] != u.k || u.k < 1) {
+                rc = fail(g, BC_ERR_ARG, "vertex update edges out of range");
+                break;
+            }
+            for (int32_t j = 0; j < u.k; ++j) {
+                const VEdge& e = g->h_entries[g->staged_first[i] + j];
+                tmp.push_back({e.x, e.dir, e.w});
+            }
+            uu.first = 0;
+        }
+        int32_t v = -1;
+        rc = validate_update(g, uu, tmp.data(), (int64_t)tmp.size(), &v, ent);
+        if (rc) break;
+        rc = enqueue_update(g, v, ent, g->d_entries + g->staged_first[i]);
+        if (rc) break;
+        ++done;
+    }
+    if (n_done) *n_done = done;
+    cudaEventRecord(g->ev_done, g->d.st);
+    return rc;
+}
+
+int bc_synchronize(bc_graph* g) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    return sync_check(g);
+}
+
+int bc_query(bc_graph* g, int32_t* done) {
+    int rc;
+    if (!done) return fail(g, BC_ERR_ARG, "done is NULL");
+    *done = 0;
+    if (!check_alive(g, &rc)) return rc;
+    cudaError_t e = cudaEventQuery(g->ev_done);
+    if (e == cudaErrorNotReady) return BC_OK;
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaEventQuery");
+    *done = 1;
+    return sync_check(g);
+}
+
+int bc_apply_updates(bc_graph* g, int32_t count, const bc_update* ups, const bc_vedge* edges,
+                     int64_t n_edges, int32_t* n_done) {
+    if (n_done) *n_done = 0;
+    int rc = bc_stage_updates(g, count, ups, edges, n_edges);
+    if (rc) return rc;
+    rc = bc_run_staged(g, n_done);
+    const int rs = bc_synchronize(g);
+    return rc ? rc : rs;
+}
+
+int bc_apply_edge_update(bc_graph* g, int32_t u, int32_t v, int64_t w_new) {
+    bc_update up{BC_UPD_EDGE, u, v, 0, w_new, 0};
+    return bc_apply_updates(g, 1, &up, nullptr, 0, nullptr);
+}
+
+int bc_apply_vertex_update(bc_graph* g, int32_t v, int32_t k, const int32_t* nbr, const int64_t* w_new,
+                           const uint8_t* dir) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (k < 1 || !nbr || !w_new || (g->directed && !dir)) return fail(g, BC_ERR_ARG, "bad vertex update arrays");
+    std::vector<bc_vedge> e(k);
+    for (int32_t j = 0; j < k; ++j) e[j] = {nbr[j], dir ? (int32_t)dir[j] : 0, w_new[j]};
+    bc_update up{BC_UPD_VERTEX, -1, v, k, 0, 0};
+    return bc_apply_updates(g, 1, &up, e.data(), k, nullptr);
+}
+
+int bc_get_scores(bc_graph* g, double* out) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (!out) return fail(g, BC_ERR_ARG, "out is NULL");
+    if ((rc = sync_check(g))) return rc;
+    std::vector<double> hi(g->n), lo(g->n);
+    CK(g, cudaMemcpy(hi.data(), g->d.bc_hi, sizeof(double) * g->n, cudaMemcpyDeviceToHost));
+    CK(g, cudaMemcpy(lo.data(), g->d.bc_lo, sizeof(double) * g->n, cudaMemcpyDeviceToHost));
+    const double f = g->directed ? 1.0 : 0.5;
+    for (int32_t t = 0; t < g->n; ++t) out[t] = (hi[t] + lo[t]) * f;
+    return BC_OK;
+}
+
+int bc_get_rows(bc_graph* g, int32_t s0, int32_t count, int64_t* d_out, uint64_t* sigma_out,
+                double* delta_out) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (s0 < 0 || count < 0 || s0 + count > g->n) return fail(g, BC_ERR_ARG, "rows out of range");
+    if ((rc = sync_check(g))) return rc;
+    const size_t n = (size_t)g->n, off = (size_t)s0 * n, cnt = (size_t)count * n;
+    if (d_out) {
+        if (g->dbytes == 8) {
+            CK(g, cudaMemcpy(d_out, (int64_t*)g->d.D + off, cnt * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<int32_t> tmp(cnt);
+            CK(g, cudaMemcpy(tmp.data(), (int32_t*)g->d.D + off, cnt * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < cnt; ++i) d_out[i] = tmp[i] == INT32_MAX ? INT64_MAX : (int64_t)tmp[i];
+        }
+    }
+    if (sigma_out) CK(g, cudaMemcpy(sigma_out, g->d.S + off, cnt * 8, cudaMemcpyDeviceToHost));
+    if (delta_out) CK(g, cudaMemcpy(delta_out, g->d.Dl + off, cnt * 8, cudaMemcpyDeviceToHost));
+    return BC_OK;
+}
+
+int bc_get_info(bc_graph* g, bc_info* out) {
+    if (!g || !out) return BC_ERR_ARG;
+    CK(g, cudaStreamSynchronize(g->d.st));
+    CK(g, cudaMemcpy(g->h_stats, g->d.stats, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    out->n = g->n;
+    out->directed = g->directed ? 1 : 0;
+    out->dist_bytes = g->dbytes;
+    out->m = (int64_t)g->wmap.size();
+    out->estar_arcs = g->estar_arcs;
+    out->rows_reaccumulated = g->h_stats[0];
+    out->noop_updates = g->h_stats[1];
+    out->max_rows = g->h_stats[2];
+    out->updates_applied = g->h_stats[3];
+    out->state_bytes = g->bytes;
+    out->last_init_ms = g->last_init_ms;
+    return BC_OK;
+}
+
+int bc_set_option(bc_graph* g, const char* name, int64_t value) {
+    if (!g || !name) return BC_ERR_ARG;
+    if (std::strcmp(name, "full_scan") == 0) {
+        g->full_scan = value != 0;
+        return BC_OK;
+    }
+    return fail(g, BC_ERR_ARG, std::string("unknown option ") + name);
+}
+
+void bc_destroy(bc_graph* g) { destroy_all(g); }
+
+const char* bc_last_error(const bc_graph* g) {
+    return g ? g->last_error.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

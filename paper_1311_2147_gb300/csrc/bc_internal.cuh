@@ -1,0 +1,161 @@
+// bc_internal.cuh -- device-side types, exact integer helpers and the launch
+// functions shared by the translation units of libbcgpu.so.
+//
+// State layout (row-major n x n, structure of arrays; Section 5 stores the triple
+// (d, sigma, flag) per pair in one row-major array -- here each field is its own
+// array so a pass reads only the fields it needs):
+//   D   [n*n]  distance type DT (int32 or int64), INF = DT max
+//   S   [n*n]  uint64 path counts sigma_st
+//   Dl  [n*n]  fp64 dependencies delta_s.(t), 0 on the diagonal
+//   BC  [n]    fp64 pair (hi, lo): compensated running sums of the G_D scores
+// E* superset ("E*+") -- every arc that lies on some shortest path, plus arcs that
+// may no longer do so (Section 6: any superset of E* gives the right DAGs) -- is a
+// CSR with per-vertex slack: arcs of vertex a sit in slots [off[a], off[a]+len[a]),
+// the slots up to off[a+1] are free (dst = -1).  src[] repeats the tail of each slot
+// so that a pass can run over the slots without the offsets.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bcg {
+
+enum : int32_t { ERRF_OVERFLOW = 1, ERRF_DIST = 2, ERRF_TIMEOUT = 4 };
+
+// Saturation marker for a distance sum that does not fit: INT64_MAX.  For DT =
+// int64 this equals INF, so callers test for it before comparing.
+constexpr int64_t SAT = INT64_MAX;
+
+template <typename DT> struct Inf;
+template <> struct Inf<int32_t> { static constexpr int64_t v = INT32_MAX; };
+template <> struct Inf<int64_t> { static constexpr int64_t v = INT64_MAX; };
+
+// a + b for finite non-negative a, b; SAT when the sum is not a finite DT value.
+template <typename DT>
+__device__ __forceinline__ int64_t dsum(int64_t a, int64_t b) {
+    if constexpr (sizeof(DT) == 4) {
+        int64_t s = a + b;
+        return s >= Inf<int32_t>::v ? SAT : s;
+    } else {
+        return (b > INT64_MAX - 1 - a) ? SAT : a + b;
+    }
+}
+
+__device__ __forceinline__ void set_err(int32_t* err, int32_t f) { atomicOr(err, f); }
+
+// Block-uniform read of the sticky error word: other CTAs of the same launch may set it
+// at any time, so kernels that use barriers take one decision for the whole CTA.
+// Every thread of the block must call it.
+__device__ __forceinline__ bool block_err(const int32_t* err) {
+    __shared__ int32_t s_err;
+    __syncthreads();
+    if (threadIdx.x == 0) s_err = *reinterpret_cast<const volatile int32_t*>(err);
+    __syncthreads();
+    return s_err != 0;
+}
+
+// 64 x 64 -> 64 product of path counts; flags overflow when the high word is used.
+__device__ __forceinline__ uint64_t mul_chk(uint64_t a, uint64_t b, int32_t* err) {
+    if (__umul64hi(a, b) != 0ull) set_err(err, ERRF_OVERFLOW);
+    return a * b;
+}
+
+__device__ __forceinline__ uint64_t add_chk(uint64_t a, uint64_t b, int32_t* err) {
+    uint64_t s = a + b;
+    if (s < a) set_err(err, ERRF_OVERFLOW);
+    return s;
+}
+
+// One edge of a vertex update, as staged on the device (matches bc_vedge).
+struct VEdge {
+    int32_t x;
+    int32_t dir;
+    int64_t w;
+};
+
+// One write into the E*+ CSR (slot < 0: only the length of vertex a changes).
+struct EOp {
+    int32_t slot;
+    int32_t a;
+    int32_t b;
+    int32_t len_a;
+    int64_t w;
+};
+constexpr int kMaxEOps = 64;
+struct EOps {
+    int32_t count;
+    int32_t pad;
+    EOp op[kMaxEOps];
+};
+
+// Device state of one handle (plain pointers; owned by the host-side bc_graph).
+struct Dev {
+    int32_t n;
+    int32_t dbytes;      // 4 or 8
+    int32_t directed;
+    int32_t nsm;
+    void* D;
+    uint64_t* S;
+    double* Dl;
+    double* bc_hi;
+    double* bc_lo;
+    // full graph (G or G_D) CSR, used by the static computation
+    int32_t* g_off;
+    int32_t* g_src;
+    int32_t* g_dst;
+    void* g_w;
+    int64_t g_arcs;
+    // E*+ CSR with slack
+    int32_t* e_off;
+    int32_t* e_len;
+    int32_t* e_src;
+    int32_t* e_dst;
+    void* e_w;
+    int64_t e_cap;
+    // error word, counters
+    int32_t* err;
+    int64_t* stats;      // [0] rows re-accumulated [1] no-op updates [2] max rows [3] updates
+    // scratch
+    uint8_t* mark;       // [n] rows that change in the current phase
+    uint8_t* changed;    // [n] rows that changed in any phase of the current update
+    int32_t* rows;       // [n] compacted rows of the current phase
+    int32_t* acc_rows;   // [n] compacted rows to re-accumulate
+    int32_t* counts;     // [0] phase rows [1] accumulation rows
+    void* fD;            // [n] per-row distance to v after the phase (DT)
+    uint64_t* fS;        // [n] per-row path count to v after the phase
+    uint64_t* fM;        // [n] per-row multiplier of a tie
+    void* cD;            // [n] per-column distances from v (DT)
+    uint64_t* cS;        // [n] per-column path counts from v
+    uint64_t* cM;        // [n] per-column multiplier of a tie
+    double* partial;     // [nrb * n] column partial sums
+    int32_t nrb_max;     // row blocks of the BC reduction
+    int32_t acc_grid;    // CTAs of the accumulation kernel
+    int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
+    int64_t ws_stride;
+    cudaStream_t st;
+};
+
+constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction
+constexpr int kAccThreads = 512;
+
+// ---- launches (k_update.cu) ----
+void launch_estar_write(const Dev& d, const EOps& ops);
+void launch_alg4_in(const Dev& d, int32_t v, const VEdge* e, int32_t k);
+void launch_rows_out(const Dev& d, int32_t v, const VEdge* e, int32_t k);
+void launch_alg4_out(const Dev& d, int32_t v, const VEdge* e, int32_t k);
+void launch_compact(const Dev& d, const uint8_t* mark, int clear, int32_t* rows,
+                    int32_t* count, int full, int stats);
+void launch_scan_in(const Dev& d, int32_t v);
+void launch_scan_out(const Dev& d, int32_t v);
+void launch_write_row(const Dev& d, int32_t v);
+void launch_estar_keep(const Dev& d, uint8_t* keep);
+
+// ---- launches (k_accum.cu) ----
+void launch_accum(const Dev& d, int is_static);
+void launch_bc_rows(const Dev& d, int sign, int is_static);
+
+// ---- launches (k_static.cu) ----
+void launch_sssp(const Dev& d);
+void launch_estar_flags(const Dev& d, uint8_t* flags);
+
+}  // namespace bcg
