@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of incremental betweenness centrality on one GB300.
+
+Default workload: undirected Barabasi-Albert graph, n = 16384, 8 edges per new vertex
+(m = 131,036 edges), weights U[1,100], and a seeded stream of 1024 incremental updates
+(half edge updates -- half new edges, half weight decreases --, half vertex updates on
+2..16 incident edges).  int32 distances, uint64 path counts, fp64 dependencies and BC.
+
+A "step" applies the next ``--per-step`` updates of the stream (each update is the
+whole hot path: Algorithm 4 passes, the rank-1 pass of Lemma 2 / 4, DAG rebuild and
+re-accumulation of every changed source, BC update).  Reported:
+  value  updates/s, device time (CUDA events on the library's stream) of K steps whose
+         update batch is already staged in device memory;
+  e2e    the same K steps through the public C-ABI call with host buffers (one
+         bc_apply_updates call per update, so p50/p99 latency per update), plus a
+         read of the BC vector after each step;
+  roofline of the dominant kernel class (events around each launch, second pass over
+         further steps), the GPU full-recompute baseline (bc_init_static on the final
+         graph) and the CPU oracle on a bounded sample of sources.
+With --impl reference the CPU oracle (static Brandes recomputed after an update) is
+timed instead, on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "edge updates/sec at n=16384 vs GPU full recompute; HBM GB/s; p50/p99 ms"
+UNIT = "updates/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+def workload(name: str):
+    from paper_1311_2147_gb300 import synth
+    if name == "ba16384":
+        g, ups = synth.workload_ba16384()
+        return g, ups, "i32", ("BA n=16384, 8 edges/vertex (m=131036), w~U[1,100], 1024 updates: "
+                               "256 new edges, 256 decreases, 512 vertex updates k~U{2..16}")
+    if name == "er256":
+        g, ups = synth.workload_er256()
+        return g, ups, "i64", "directed ER n=256 m=2048, w~U[1,1000], 16 updates"
+    if name == "complete2048":
+        g, ups = synth.workload_complete2048()
+        return g, ups, "i64", "complete directed n=2048, w~U{1..n^2}, 256 weight decreases"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def read_traffic(kernel_class: str, workload_name: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, if the kernel
+    source is unchanged since it was captured (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_class}_{workload_name}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln and ln.strip().startswith("- "):
+                k, v = ln.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    src = vals.get("source_file")
+    sha = vals.get("source_sha256")
+    if not src or not sha or "traffic_bytes_per_launch" not in vals:
+        return None
+    fp = os.path.join(ROOT, src)
+    if not os.path.exists(fp) or hashlib.sha256(open(fp, "rb").read()).hexdigest() != sha:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
+
+
+def cpu_oracle_rate(g, sample_sources: int, seed: int = 7):
+    """Static Brandes (the oracle as it stands) from a sample of sources on all host cores,
+    scaled to one full recompute; returns (updates/s, seconds, cores, sources)."""
+    from oracle import oracle
+    from paper_1311_2147_gb300 import synth
+    n = g.n
+    k = min(sample_sources, n)
+    srcs = np.sort(synth.Rng(seed).below(n, k)).astype(np.int32)
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.brandes(g, sources=srcs, want_rows=False, want_bc=True, nthreads=cores)
+    dt = time.perf_counter() - t0
+    full = dt * n / k
+    return 1.0 / full, dt, cores, k
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1311_2147_gb300 import synth
+    g, ups, dist, desc = workload(args.workload)
+    W, K = args.warmup, args.steps
+    em = synth.EdgeMap.of(g)
+    times = []
+    cores = None
+    sample = args.cpu_sample
+    for step in range(W + K):
+        up = ups[step % len(ups)]
+        synth.apply_update(em, up)
+        gg = em.to_graph()
+        rate, dt, cores, k = cpu_oracle_rate(gg, sample, seed=step)
+        if step >= W:
+            times.append(1.0 / rate)
+    value = K / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * sum(times) / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64/u64/f64", "data": "synthetic",
+            "config": {"workload": desc, "updates_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: static Brandes from {sample} seeded sources of the "
+                                       f"updated graph on {cores} threads, scaled by n/{sample} to one "
+                                       f"full recompute after that update"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1311_2147_gb300 import binding, synth
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    binding.load()
+    g, ups, dtype, desc = workload(args.workload)
+    n = g.n
+    U, W, K = args.per_step, args.warmup, args.steps
+    need = (W + 2 * K) * U
+    if need > len(ups):
+        raise SystemExit(f"stream has {len(ups)} updates, need {need}: lower --per-step/--steps")
+    sl = [ups[i * U:(i + 1) * U] for i in range((W + 2 * K))]
+    sd = 4 if dtype == "i32" else 8
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------- value: device time, update batches resident before timing
+    A = binding.BCGraph(g, dist=dtype, stream=stream.cuda_stream)
+    for i in range(W):
+        rc, done = A.bc_apply_updates(sl[i])
+        assert rc == 0, A.last_error()
+    timed = [u for s in sl[W:W + K] for u in s]
+    assert A.bc_stage_updates(timed) == 0
+    info0 = A.bc_get_info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        rc, done = A.bc_run_staged()
+        e1.record(stream)
+        assert rc == 0 and done == len(timed), A.last_error()
+        assert A.bc_synchronize() == 0, A.last_error()
+        barrier()
+    dev_ms = e0.elapsed_time(e1)
+    info1 = A.bc_get_info()
+    launches = info1["kernel_launches"] - info0["kernel_launches"]
+    t_max = dev_ms
+    if dist is not None:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * len(timed) / (t_max / 1e3)
+
+    # ---------------- per-kernel-class profile over the next K steps (events per launch)
+    A.bc_set_option("profile", 1)
+    A.bc_get_profile(reset=True)
+    infop0 = A.bc_get_info()
+    prof_updates = [u for s in sl[W + K:W + 2 * K] for u in s]
+    rc, done = A.bc_apply_updates(prof_updates)
+    assert rc == 0, A.last_error()
+    prof = A.bc_get_profile(reset=True)
+    infop1 = A.bc_get_info()
+    A.bc_set_option("profile", 0)
+    d_rows_acc = infop1["rows_reaccumulated"] - infop0["rows_reaccumulated"]
+    d_rows_scan = infop1["rows_scanned"] - infop0["rows_scanned"]
+    d_low = infop1["pairs_lowered"] - infop0["pairs_lowered"]
+    d_tie = infop1["pairs_tied"] - infop0["pairs_tied"]
+    # algorithmic HBM bytes per kernel class over the profiled steps
+    alg_bytes = {
+        # rank-1 pass: read d of every scanned pair, sigma read+write on ties, d+sigma
+        # written where the distance drops
+        "scan": d_rows_scan * n * sd + d_tie * 16 + d_low * (sd + 8),
+        # accumulation: per re-accumulated source its d row, sigma row and new delta row
+        "accumulate": d_rows_acc * n * (sd + 8 + 8),
+        # BC row sums: the changed delta rows are read twice (before and after)
+        "bc_rows": 2 * d_rows_acc * n * 8,
+    }
+    peak, peak_kind = load_peaks()
+    dom = max(prof, key=lambda c: prof[c][0])
+    dom_ms, dom_launches = prof[dom]
+    roof = None
+    if dom in alg_bytes and dom_launches > 0 and dom_ms > 0:
+        per_launch = alg_bytes[dom] / dom_launches
+        achieved = alg_bytes[dom] / (dom_ms / 1e3) / 1e9
+        traffic = read_traffic(dom, args.workload)
+        roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": per_launch, "traffic": traffic,
+                "launches": dom_launches, "avg_launch_ms": dom_ms / dom_launches}
+    classes = {c: {"ms": prof[c][0], "launches": prof[c][1],
+                   "gbs": (alg_bytes[c] / (prof[c][0] / 1e3) / 1e9) if c in alg_bytes and prof[c][0] > 0 else None}
+               for c in prof}
+    A.close()
+
+    # ---------------- e2e through the C-ABI with host buffers, per-update latency
+    e2e = None
+    lat = []
+    if not args.no_e2e:
+        B = binding.BCGraph(g, dist=dtype, stream=stream.cuda_stream)
+        for i in range(W):
+            rc, _ = B.bc_apply_updates(sl[i])
+            assert rc == 0
+        barrier()
+        h2d = 0
+        d2h = 0
+        t0 = time.perf_counter()
+        for s in sl[W:W + K]:
+            for up in s:
+                rec, ed = binding.encode_updates([up])
+                h2d += rec.nbytes + ed.nbytes
+                d2h += 4
+                ta = time.perf_counter()
+                rc, _ = B.bc_apply_updates((rec, ed))
+                lat.append(1e3 * (time.perf_counter() - ta))
+                assert rc == 0, B.last_error()
+            scores = B.bc_get_scores()
+            d2h += 2 * scores.nbytes
+        barrier()
+        wall = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        e2e = {"value": world * len(timed) / wall, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
+               "d2h_bytes_per_step": d2h // K, "p50_ms": float(np.percentile(lat, 50)),
+               "p99_ms": float(np.percentile(lat, 99))}
+        B.close()
+
+    # ---------------- baselines: GPU full recompute and the CPU oracle (rank 0 only)
+    gpu_full = None
+    cpu = None
+    if rank == 0 and not args.no_baselines:
+        gfin = synth.apply_updates(g, ups[:(W + 2 * K) * U])
+        ms = []
+        for _ in range(args.recompute_runs):
+            C = binding.BCGraph(gfin, dist=dtype, stream=stream.cuda_stream)
+            ms.append(C.bc_get_info()["last_init_ms"])
+            C.close()
+        med = statistics.median(ms)
+        gpu_full = {"ms": med, "runs": ms, "updates_per_s": 1e3 / med,
+                    "incremental_speedup": value / world / (1e3 / med)}
+        if world == 1:
+            rate, dt, cores, k = cpu_oracle_rate(gfin, args.cpu_sample)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"static Brandes from {k} seeded sources of the final graph ({dt:.1f} s on "
+                             f"{cores} threads), scaled by n/{k} to one full recompute per update"}
+
+    if rank == 0:
+        rows_per_upd = (info1["rows_reaccumulated"] - info0["rows_reaccumulated"]) / len(timed)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32/u64/f64" if dtype == "i32" else "int64/u64/f64", "data": "synthetic",
+                "config": {"workload": desc, "updates_per_step": U,
+                           "l2": f"state {n * n * (sd + 16) / 1e9:.2f} GB per graph > 129 MB L2; no flush",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clk.summary(), "gpu_full_recompute": gpu_full,
+                "latency_ms": {"p50": e2e["p50_ms"], "p99": e2e["p99_ms"]} if e2e else None,
+                "classes": classes, "rows_per_update": rows_per_upd}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--per-step", type=int, default=32)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ba16384", choices=["ba16384", "er256", "complete2048"])
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--recompute-runs", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

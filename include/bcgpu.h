@@ -107,6 +107,10 @@ typedef struct bc_info {
     int64_t rows_reaccumulated;  /* sum over updates of the sources re-accumulated */
     int64_t noop_updates;        /* updates that changed no pair */
     int64_t max_rows;            /* largest number of sources of one update */
+    int64_t rows_scanned;        /* rows passed through the rank-1 pass (all phases) */
+    int64_t pairs_lowered;       /* pairs whose distance dropped (Lemma 2/4 last case) */
+    int64_t pairs_tied;          /* pairs that gained tied shortest paths */
+    int64_t kernel_launches;     /* kernels enqueued by this handle since init */
     int64_t state_bytes;         /* device bytes owned by the handle */
     double last_init_ms;         /* device time of the static computation in bc_init_static */
 } bc_info;
@@ -118,7 +122,7 @@ typedef struct bc_info {
  * 2-4), then Algorithm 1 for every source).  This is also the GPU full-recompute
  * baseline.
  *   out          receives the new handle (NULL on failure).
- *   n            number of vertices (1 .. 65536).
+ *   n            number of vertices (1 .. 32768).
  *   m            number of edges in src/dst/w (undirected: each edge once).
  *   src,dst,w    host arrays of m entries; w in [1, INF-1] of the distance type.
  *   flags        exactly one of BC_DIRECTED / BC_UNDIRECTED, and one of
@@ -208,9 +212,22 @@ int bc_get_rows(bc_graph* g, int32_t s0, int32_t count, int64_t* d_out,
 int bc_get_info(bc_graph* g, bc_info* out);
 
 /*
+ * bc_get_profile -- device time in ms and kernel launches per kernel class, summed over
+ * the updates enqueued while the "profile" option was on (CUDA events recorded around
+ * each launch on the handle's stream).  Classes: 0 the rank-1 pass (Lemma 2 / 4),
+ * 1 dependency accumulation (Eq. 4 / Algorithm 1), 2 BC row sums, 3 per-vertex passes
+ * (Algorithm 4 in both directions, row tests, row write), 4 bookkeeping (compaction,
+ * E* writes).  ms and launches are host arrays of BC_PROFILE_CLASSES entries (either
+ * may be NULL).  reset != 0 clears the sums after reading.  Synchronous.
+ */
+enum { BC_PROFILE_CLASSES = 5 };
+int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
+
+/*
  * bc_set_option -- tuning knobs (documented values only):
  *   "full_scan" 0|1: run the rank-1 pass of Lemma 2 / 4 over every row instead of
  *                     only the rows that can change (Section 5 scans all n^2 pairs).
+ *   "profile"   0|1: record CUDA events around every launch (see bc_get_profile).
  */
 int bc_set_option(bc_graph* g, const char* name, int64_t value);
 

@@ -39,7 +39,8 @@ INF64 = np.iinfo(np.int64).max
 
 EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "bc_apply_updates",
            "bc_stage_updates", "bc_run_staged", "bc_synchronize", "bc_query", "bc_get_scores",
-           "bc_get_rows", "bc_get_info", "bc_set_option", "bc_destroy", "bc_last_error"]
+           "bc_get_rows", "bc_get_info", "bc_get_profile", "bc_set_option", "bc_destroy", "bc_last_error"]
+PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping"]
 
 
 class bc_info(ctypes.Structure):
@@ -47,6 +48,8 @@ class bc_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("m", ctypes.c_int64), ("estar_arcs", ctypes.c_int64),
                 ("updates_applied", ctypes.c_int64), ("rows_reaccumulated", ctypes.c_int64),
                 ("noop_updates", ctypes.c_int64), ("max_rows", ctypes.c_int64),
+                ("rows_scanned", ctypes.c_int64), ("pairs_lowered", ctypes.c_int64),
+                ("pairs_tied", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double)]
 
 
@@ -87,6 +90,7 @@ def load(build_if_missing: bool = True):
         "bc_get_scores": ([p, p], ctypes.c_int),
         "bc_get_rows": ([p, i32, i32, p, p, p], ctypes.c_int),
         "bc_get_info": ([p, ctypes.POINTER(bc_info)], ctypes.c_int),
+        "bc_get_profile": ([p, p, p, i32], ctypes.c_int),
         "bc_set_option": ([p, ctypes.c_char_p, i64], ctypes.c_int),
         "bc_destroy": ([p], None),
         "bc_last_error": ([p], ctypes.c_char_p),
@@ -215,6 +219,12 @@ class BCGraph:
         info = bc_info()
         self._check(self.lib.bc_get_info(self.h, ctypes.byref(info)))
         return {k: getattr(info, k) for k, _ in bc_info._fields_}
+
+    def bc_get_profile(self, reset=True):
+        ms = np.zeros(len(PROFILE_CLASSES), np.float64)
+        nl = np.zeros(len(PROFILE_CLASSES), np.int64)
+        self._check(self.lib.bc_get_profile(self.h, _ptr(ms), _ptr(nl), 1 if reset else 0))
+        return {c: (float(ms[i]), int(nl[i])) for i, c in enumerate(PROFILE_CLASSES)}
 
     def last_error(self):
         return self.lib.bc_last_error(self.h).decode()

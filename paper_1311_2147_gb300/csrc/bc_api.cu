@@ -19,7 +19,7 @@ thread_local std::string g_init_error;
 
 inline uint64_t arc_key(int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
 
-struct Arc {
+struct HArc {
     int32_t a, b;
     int64_t w;
 };
@@ -55,10 +55,23 @@ struct bc_graph {
     int64_t* h_stats = nullptr;           // pinned
     uint8_t* d_keep = nullptr;
     int64_t d_keep_cap = 0;
+    int64_t big_cap = 0;
+    int64_t ws_cap = 0;
     cudaEvent_t ev_done = nullptr;
     int64_t bytes = 0;
     double last_init_ms = 0.0;
     std::vector<void*> allocs;
+    // launch accounting and optional per-class event timing
+    int64_t launches = 0;
+    bool profile = false;
+    struct Rec {
+        cudaEvent_t a, b;
+        int cls, nl;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[BC_PROFILE_CLASSES] = {0};
+    int64_t prof_launches[BC_PROFILE_CLASSES] = {0};
 };
 
 namespace {
@@ -115,9 +128,48 @@ const char* status_text(int s) {
     }
 }
 
+cudaEvent_t take_event(bc_graph* g) {
+    if (!g->pool.empty()) {
+        cudaEvent_t e = g->pool.back();
+        g->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Run one group of nl launches of kernel class cls, timed with events when profiling.
+template <typename F>
+void timed(bc_graph* g, int cls, int nl, F&& fn) {
+    g->launches += nl;
+    if (!g->profile) {
+        fn();
+        return;
+    }
+    cudaEvent_t a = take_event(g), b = take_event(g);
+    cudaEventRecord(a, g->d.st);
+    fn();
+    cudaEventRecord(b, g->d.st);
+    g->pending.push_back({a, b, cls, nl});
+}
+
+// Fold finished event pairs into the per-class sums (the stream has been synchronised).
+void collect_profile(bc_graph* g) {
+    for (auto& r : g->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) g->prof_ms[r.cls] += ms;
+        g->prof_launches[r.cls] += r.nl;
+        g->pool.push_back(r.a);
+        g->pool.push_back(r.b);
+    }
+    g->pending.clear();
+}
+
 // Wait for the stream and turn a device-side error into a status (poisoning the handle).
 int sync_check(bc_graph* g) {
     CK(g, cudaStreamSynchronize(g->d.st));
+    collect_profile(g);
     CK(g, cudaMemcpy(g->h_err, g->d.err, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (*g->h_err) {
         g->poisoned = true;
@@ -128,10 +180,10 @@ int sync_check(bc_graph* g) {
 }
 
 // Lay the E* superset out with slack per vertex and upload it.
-int estar_layout(bc_graph* g, const std::vector<Arc>& arcs) {
+int estar_layout(bc_graph* g, const std::vector<HArc>& arcs) {
     const int32_t n = g->n;
     std::vector<int32_t> deg(n, 0);
-    for (const Arc& x : arcs) deg[x.a]++;
+    for (const HArc& x : arcs) deg[x.a]++;
     g->e_off.assign(n + 1, 0);
     g->e_len.assign(n, 0);
     for (int32_t a = 0; a < n; ++a) g->e_off[a + 1] = g->e_off[a] + deg[a] + 2 + deg[a] / 8;
@@ -141,7 +193,7 @@ int estar_layout(bc_graph* g, const std::vector<Arc>& arcs) {
     g->e_w.assign(cap, 0);
     g->eslot.clear();
     g->eslot.reserve(arcs.size() * 2 + 16);
-    for (const Arc& x : arcs) {
+    for (const HArc& x : arcs) {
         const int32_t slot = g->e_off[x.a] + g->e_len[x.a]++;
         g->e_src[slot] = x.a;
         g->e_dst[slot] = x.b;
@@ -152,51 +204,68 @@ int estar_layout(bc_graph* g, const std::vector<Arc>& arcs) {
         for (int32_t s = g->e_off[a]; s < g->e_off[a + 1]; ++s) g->e_src[s] = a;
     g->estar_arcs = (int64_t)arcs.size();
     Dev& d = g->d;
+    const size_t asz = g->dbytes == 4 ? sizeof(Arc<int32_t>) : sizeof(Arc<int64_t>);
     if (cap > d.e_cap) {
         dfree(g, d.e_src);
-        dfree(g, d.e_dst);
-        dfree(g, d.e_w);
-        d.e_src = d.e_dst = nullptr;
-        d.e_w = nullptr;
+        dfree(g, d.e_arc);
+        d.e_src = nullptr;
+        d.e_arc = nullptr;
         const int64_t ncap = cap + cap / 4 + 64;
         int rc;
-        if ((rc = dalloc(g, &d.e_src, ncap)) || (rc = dalloc(g, &d.e_dst, ncap))) return rc;
-        if (g->dbytes == 4) {
-            int32_t* p;
-            if ((rc = dalloc(g, &p, ncap))) return rc;
-            d.e_w = p;
-        } else {
-            int64_t* p;
-            if ((rc = dalloc(g, &p, ncap))) return rc;
-            d.e_w = p;
-        }
+        if ((rc = dalloc(g, &d.e_src, ncap))) return rc;
+        unsigned char* p = nullptr;
+        if ((rc = dalloc(g, &p, ncap * asz))) return rc;
+        d.e_arc = p;
         d.e_cap = ncap;
     }
+    // vertices whose segments are walked by a whole warp
+    std::vector<int32_t> big;
+    for (int32_t a = 0; a < n; ++a)
+        if (g->e_off[a + 1] - g->e_off[a] > kSmallDeg) big.push_back(a);
+    if ((int64_t)big.size() > g->big_cap) {
+        dfree(g, d.e_big);
+        d.e_big = nullptr;
+        int rc;
+        if ((rc = dalloc(g, &d.e_big, big.size()))) return rc;
+        g->big_cap = (int64_t)big.size();
+    }
+    d.e_nbig = (int32_t)big.size();
     // free slots beyond the layout stay empty (dst = -1)
-    std::vector<int32_t> dst_full(d.e_cap, -1), src_full(d.e_cap, 0);
-    std::copy(g->e_dst.begin(), g->e_dst.end(), dst_full.begin());
+    std::vector<int32_t> src_full(d.e_cap, 0);
     std::copy(g->e_src.begin(), g->e_src.end(), src_full.begin());
+    std::vector<unsigned char> arc_bytes(d.e_cap * asz);
+    if (g->dbytes == 4) {
+        Arc<int32_t>* A = reinterpret_cast<Arc<int32_t>*>(arc_bytes.data());
+        for (int64_t i = 0; i < d.e_cap; ++i)
+            A[i] = i < cap ? Arc<int32_t>{g->e_dst[i], (int32_t)g->e_w[i]} : Arc<int32_t>{-1, 0};
+    } else {
+        Arc<int64_t>* A = reinterpret_cast<Arc<int64_t>*>(arc_bytes.data());
+        for (int64_t i = 0; i < d.e_cap; ++i)
+            A[i] = i < cap ? Arc<int64_t>{(int64_t)g->e_dst[i], g->e_w[i]} : Arc<int64_t>{-1, 0};
+    }
     CK(g, cudaMemcpyAsync(d.e_off, g->e_off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, d.st));
     CK(g, cudaMemcpyAsync(d.e_len, g->e_len.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, d.st));
     CK(g, cudaMemcpyAsync(d.e_src, src_full.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
-    CK(g, cudaMemcpyAsync(d.e_dst, dst_full.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
-    if (g->dbytes == 4) {
-        std::vector<int32_t> w32(d.e_cap, 0);
-        for (int64_t i = 0; i < cap; ++i) w32[i] = (int32_t)g->e_w[i];
-        CK(g, cudaMemcpyAsync(d.e_w, w32.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
-        CK(g, cudaStreamSynchronize(d.st));
-    } else {
-        std::vector<int64_t> w64(d.e_cap, 0);
-        std::copy(g->e_w.begin(), g->e_w.end(), w64.begin());
-        CK(g, cudaMemcpyAsync(d.e_w, w64.data(), sizeof(int64_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
-        CK(g, cudaStreamSynchronize(d.st));
+    CK(g, cudaMemcpyAsync(d.e_arc, arc_bytes.data(), arc_bytes.size(), cudaMemcpyHostToDevice, d.st));
+    if (!big.empty())
+        CK(g, cudaMemcpyAsync(d.e_big, big.data(), sizeof(int32_t) * big.size(), cudaMemcpyHostToDevice, d.st));
+    CK(g, cudaStreamSynchronize(d.st));
+    // launch shape of the accumulation depends on the capacity: size its work space
+    accum_config(d);
+    const int64_t need = (int64_t)d.acc_grid * d.ws_stride;
+    if (need > g->ws_cap) {
+        dfree(g, d.ws);
+        d.ws = nullptr;
+        int rc;
+        if ((rc = dalloc(g, &d.ws, need))) return rc;
+        g->ws_cap = need;
     }
     return BC_OK;
 }
 
 // Rebuild the E* superset when a vertex runs out of slack: keep the arcs that are still
 // in E* (w = d), add the pending arcs, lay out again.
-int estar_rebuild(bc_graph* g, const std::vector<Arc>& pending) {
+int estar_rebuild(bc_graph* g, const std::vector<HArc>& pending) {
     int rc = sync_check(g);
     if (rc) return rc;
     Dev& d = g->d;
@@ -211,8 +280,8 @@ int estar_rebuild(bc_graph* g, const std::vector<Arc>& pending) {
     CK(g, cudaMemcpyAsync(keep.data(), g->d_keep, d.e_cap, cudaMemcpyDeviceToHost, d.st));
     CK(g, cudaStreamSynchronize(d.st));
     std::unordered_set<uint64_t> pend;
-    for (const Arc& x : pending) pend.insert(arc_key(x.a, x.b));
-    std::vector<Arc> arcs;
+    for (const HArc& x : pending) pend.insert(arc_key(x.a, x.b));
+    std::vector<HArc> arcs;
     arcs.reserve(g->estar_arcs + pending.size());
     const int64_t cap = (int64_t)g->e_dst.size();
     for (int64_t s = 0; s < cap; ++s) {
@@ -220,7 +289,7 @@ int estar_rebuild(bc_graph* g, const std::vector<Arc>& pending) {
         if (pend.count(arc_key(g->e_src[s], g->e_dst[s]))) continue;
         arcs.push_back({g->e_src[s], g->e_dst[s], g->e_w[s]});
     }
-    for (const Arc& x : pending) arcs.push_back(x);
+    for (const HArc& x : pending) arcs.push_back(x);
     return estar_layout(g, arcs);
 }
 
@@ -267,7 +336,7 @@ int validate_update(bc_graph* g, const bc_update& u, const bc_vedge* edges, int6
 // Apply a validated update to the host weights and the E* superset mirror; fills the
 // device writes to make.  Sets *rebuild when a vertex has no free slot left.
 void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::vector<EOp>& ops,
-                   std::vector<Arc>& arcs, bool* rebuild) {
+                   std::vector<HArc>& arcs, bool* rebuild) {
     arcs.clear();
     for (const VEdge& e : ent) {
         if (!g->directed) {
@@ -281,7 +350,7 @@ void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::v
     }
     *rebuild = false;
     ops.clear();
-    for (const Arc& x : arcs) {
+    for (const HArc& x : arcs) {
         g->wmap[arc_key(x.a, x.b)] = x.w;
         auto it = g->eslot.find(arc_key(x.a, x.b));
         if (it != g->eslot.end()) {
@@ -307,7 +376,7 @@ void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::v
 int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const VEdge* d_ent) {
     Dev& d = g->d;
     std::vector<EOp> ops;
-    std::vector<Arc> arcs;
+    std::vector<HArc> arcs;
     bool rebuild = false;
     mirror_update(g, v, ent, ops, arcs, &rebuild);
     if (rebuild) {
@@ -318,7 +387,7 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             EOps pack{};
             pack.count = (int32_t)std::min<size_t>(kMaxEOps, ops.size() - i);
             for (int j = 0; j < pack.count; ++j) pack.op[j] = ops[i + j];
-            launch_estar_write(d, pack);
+            timed(g, 4, 1, [&] { launch_estar_write(d, pack); });
         }
     }
     int32_t kin = 0, kout = 0;
@@ -329,21 +398,23 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
     const int32_t k = (int32_t)ent.size();
     const int full = g->full_scan ? 1 : 0;
     if (kin) {
-        launch_alg4_in(d, v, d_ent, k);
-        launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0);
-        launch_scan_in(d, v);
+        timed(g, 3, 1, [&] { launch_alg4_in(d, v, d_ent, k); });
+        timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
+        timed(g, 0, 1, [&] { launch_scan_in(d, v); });
     }
     if (kout) {
-        launch_alg4_out(d, v, d_ent, k);
-        launch_rows_out(d, v, d_ent, k);
-        launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0);
-        launch_scan_out(d, v);
-        launch_write_row(d, v);
+        timed(g, 3, 2, [&] {
+            launch_alg4_out(d, v, d_ent, k);
+            launch_rows_out(d, v, d_ent, k);
+        });
+        timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
+        timed(g, 0, 1, [&] { launch_scan_out(d, v); });
+        timed(g, 3, 1, [&] { launch_write_row(d, v); });
     }
-    launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1);
-    launch_bc_rows(d, -1, 0);
-    launch_accum(d, 0);
-    launch_bc_rows(d, +1, 0);
+    timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
+    timed(g, 2, 2, [&] { launch_bc_rows(d, -1, 0); });
+    timed(g, 1, 1, [&] { launch_accum(d, 0); });
+    timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
     CK(g, cudaGetLastError());
     return BC_OK;
 }
@@ -356,6 +427,11 @@ void destroy_all(bc_graph* g) {
     if (g->h_err) cudaFreeHost(g->h_err);
     if (g->h_stats) cudaFreeHost(g->h_stats);
     if (g->ev_done) cudaEventDestroy(g->ev_done);
+    for (auto& r : g->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : g->pool) cudaEventDestroy(e);
     delete g;
 }
 
@@ -383,7 +459,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     const bool dir = (flags & BC_DIRECTED) != 0, und = (flags & BC_UNDIRECTED) != 0;
     const bool i32 = (flags & BC_DIST_I32) != 0, i64 = (flags & BC_DIST_I64) != 0;
     if (dir == und || i32 == i64) return fail(nullptr, BC_ERR_ARG, "flags need one of DIRECTED/UNDIRECTED and one of DIST_I32/DIST_I64");
-    if (n < 1 || n > 65536) return fail(nullptr, BC_ERR_ARG, "n must be in [1, 65536]");
+    if (n < 1 || n > 32768) return fail(nullptr, BC_ERR_ARG, "n must be in [1, 32768]");
     if (m < 0 || (m > 0 && (!src || !dst || !w))) return fail(nullptr, BC_ERR_ARG, "bad edge arrays");
     bc_graph* g = new bc_graph();
     g->n = n;
@@ -405,7 +481,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     }
     // ---- arcs of G (G_D), validated
     const int64_t arcs = dir ? m : 2 * m;
-    std::vector<Arc> all;
+    std::vector<HArc> all;
     all.reserve(arcs);
     g->wmap.reserve(arcs * 2 + 16);
     for (int64_t i = 0; i < m; ++i) {
@@ -424,11 +500,11 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     // CSR of G by tail
     std::vector<int32_t> off(n + 1, 0), csrc(arcs), cdst(arcs);
     std::vector<int64_t> cw(arcs);
-    for (const Arc& x : all) off[x.a + 1]++;
+    for (const HArc& x : all) off[x.a + 1]++;
     for (int32_t a = 0; a < n; ++a) off[a + 1] += off[a];
     {
         std::vector<int32_t> pos(off.begin(), off.end() - 1);
-        for (const Arc& x : all) {
+        for (const HArc& x : all) {
             const int32_t p = pos[x.a]++;
             csrc[p] = x.a;
             cdst[p] = x.b;
@@ -438,8 +514,6 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     // ---- device memory
     const size_t nn = (size_t)n * n;
     int rc = BC_OK;
-    d.acc_grid = d.nsm * 2;
-    d.ws_stride = ((3 * (int64_t)n + 2) + 3) & ~(int64_t)3;
     d.nrb_max = (n + kRowsPerBlock - 1) / kRowsPerBlock;
     d.g_arcs = arcs;
     if (g->dbytes == 4) {
@@ -466,8 +540,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         (rc = dalloc(g, &d.changed, n)) || (rc = dalloc(g, &d.rows, n)) || (rc = dalloc(g, &d.acc_rows, n)) ||
         (rc = dalloc(g, &d.counts, 4)) || (rc = dalloc(g, &d.fS, n)) || (rc = dalloc(g, &d.fM, n)) ||
         (rc = dalloc(g, &d.cS, n)) || (rc = dalloc(g, &d.cM, n)) ||
-        (rc = dalloc(g, &d.partial, (size_t)d.nrb_max * n)) ||
-        (rc = dalloc(g, &d.ws, (size_t)d.acc_grid * d.ws_stride))) {
+        (rc = dalloc(g, &d.partial, (size_t)d.nrb_max * n))) {
         destroy_all(g);
         return fail(nullptr, rc, "device allocation failed");
     }
@@ -523,7 +596,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     dfree(g, d_flags);
     g->bytes -= (int64_t)std::max<int64_t>(arcs, 1);
     {
-        std::vector<Arc> estar;
+        std::vector<HArc> estar;
         for (int64_t i = 0; i < arcs; ++i)
             if (eflags[i]) estar.push_back({csrc[i], cdst[i], cw[i]});
         if ((rc = estar_layout(g, estar))) return bail(rc, g->last_error);
@@ -704,7 +777,11 @@ int bc_get_rows(bc_graph* g, int32_t s0, int32_t count, int64_t* d_out, uint64_t
         }
     }
     if (sigma_out) CK(g, cudaMemcpy(sigma_out, g->d.S + off, cnt * 8, cudaMemcpyDeviceToHost));
-    if (delta_out) CK(g, cudaMemcpy(delta_out, g->d.Dl + off, cnt * 8, cudaMemcpyDeviceToHost));
+    if (delta_out) {
+        std::vector<ff> tmp(cnt);
+        CK(g, cudaMemcpy(tmp.data(), g->d.Dl + off, cnt * sizeof(ff), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < cnt; ++i) delta_out[i] = ff_to_double(tmp[i]);
+    }
     return BC_OK;
 }
 
@@ -722,6 +799,10 @@ int bc_get_info(bc_graph* g, bc_info* out) {
     out->noop_updates = g->h_stats[1];
     out->max_rows = g->h_stats[2];
     out->updates_applied = g->h_stats[3];
+    out->pairs_lowered = g->h_stats[4];
+    out->pairs_tied = g->h_stats[5];
+    out->rows_scanned = g->h_stats[6];
+    out->kernel_launches = g->launches;
     out->state_bytes = g->bytes;
     out->last_init_ms = g->last_init_ms;
     return BC_OK;
@@ -733,7 +814,26 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
         g->full_scan = value != 0;
         return BC_OK;
     }
+    if (std::strcmp(name, "profile") == 0) {
+        g->profile = value != 0;
+        return BC_OK;
+    }
     return fail(g, BC_ERR_ARG, std::string("unknown option ") + name);
+}
+
+int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset) {
+    if (!g) return BC_ERR_ARG;
+    CK(g, cudaStreamSynchronize(g->d.st));
+    collect_profile(g);
+    for (int c = 0; c < BC_PROFILE_CLASSES; ++c) {
+        if (ms) ms[c] = g->prof_ms[c];
+        if (launches) launches[c] = g->prof_launches[c];
+        if (reset) {
+            g->prof_ms[c] = 0.0;
+            g->prof_launches[c] = 0;
+        }
+    }
+    return BC_OK;
 }
 
 void bc_destroy(bc_graph* g) { destroy_all(g); }

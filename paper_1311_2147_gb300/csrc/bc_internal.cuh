@@ -6,17 +6,22 @@
 // array so a pass reads only the fields it needs):
 //   D   [n*n]  distance type DT (int32 or int64), INF = DT max
 //   S   [n*n]  uint64 path counts sigma_st
-//   Dl  [n*n]  fp64 dependencies delta_s.(t), 0 on the diagonal
+//   Dl  [n*n]  dependencies delta_s.(t) as float-float pairs (ff.cuh), 0 on the diagonal
 //   BC  [n]    fp64 pair (hi, lo): compensated running sums of the G_D scores
 // E* superset ("E*+") -- every arc that lies on some shortest path, plus arcs that
 // may no longer do so (Section 6: any superset of E* gives the right DAGs) -- is a
 // CSR with per-vertex slack: arcs of vertex a sit in slots [off[a], off[a]+len[a]),
-// the slots up to off[a+1] are free (dst = -1).  src[] repeats the tail of each slot
-// so that a pass can run over the slots without the offsets.
+// the slots up to off[a+1] are free (dst = -1).  Each slot is a packed (dst, w) pair
+// (Arc<DT>: 8 bytes for int32 distances, 16 for int64) so one load brings both;
+// src[] repeats the tail of each slot for passes that run over the slots.  Vertices
+// whose segment holds more than kSmallDeg slots are listed in big[] (warp-cooperative
+// handling in the accumulation).
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "ff.cuh"
 
 namespace bcg {
 
@@ -66,6 +71,12 @@ __device__ __forceinline__ uint64_t add_chk(uint64_t a, uint64_t b, int32_t* err
     return s;
 }
 
+template <typename DT> struct Arc;
+template <> struct __align__(8) Arc<int32_t> { int32_t dst; int32_t w; };
+template <> struct __align__(16) Arc<int64_t> { int64_t dst; int64_t w; };
+
+constexpr int kSmallDeg = 32;   // segments up to this many slots are walked by one thread
+
 // One edge of a vertex update, as staged on the device (matches bc_vedge).
 struct VEdge {
     int32_t x;
@@ -96,7 +107,7 @@ struct Dev {
     int32_t nsm;
     void* D;
     uint64_t* S;
-    double* Dl;
+    ff* Dl;
     double* bc_hi;
     double* bc_lo;
     // full graph (G or G_D) CSR, used by the static computation
@@ -109,12 +120,14 @@ struct Dev {
     int32_t* e_off;
     int32_t* e_len;
     int32_t* e_src;
-    int32_t* e_dst;
-    void* e_w;
+    void* e_arc;         // Arc<DT>[e_cap]
     int64_t e_cap;
+    int32_t* e_big;      // vertices with more than kSmallDeg slots
+    int32_t e_nbig;
     // error word, counters
     int32_t* err;
     int64_t* stats;      // [0] rows re-accumulated [1] no-op updates [2] max rows [3] updates
+                         // [4] pairs lowered [5] pairs with new ties [6] rows scanned
     // scratch
     uint8_t* mark;       // [n] rows that change in the current phase
     uint8_t* changed;    // [n] rows that changed in any phase of the current update
@@ -127,9 +140,11 @@ struct Dev {
     void* cD;            // [n] per-column distances from v (DT)
     uint64_t* cS;        // [n] per-column path counts from v
     uint64_t* cM;        // [n] per-column multiplier of a tie
-    double* partial;     // [nrb * n] column partial sums
+    ff* partial;         // [nrb * n] column partial sums
     int32_t nrb_max;     // row blocks of the BC reduction
     int32_t acc_grid;    // CTAs of the accumulation kernel
+    int32_t acc_smem;    // dynamic shared memory of the accumulation kernel
+    int32_t acc_mask_smem;  // 1: the DAG slot mask lives in shared memory
     int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
     int64_t ws_stride;
     cudaStream_t st;
@@ -137,6 +152,10 @@ struct Dev {
 
 constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction
 constexpr int kAccThreads = 512;
+
+// Accumulation launch shape for n and the current E* capacity (sets acc_grid, acc_smem,
+// acc_mask_smem and ws_stride of d); the work space must then hold acc_grid * ws_stride.
+void accum_config(Dev& d);
 
 // ---- launches (k_update.cu) ----
 void launch_estar_write(const Dev& d, const EOps& ops);

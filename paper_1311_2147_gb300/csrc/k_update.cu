@@ -23,16 +23,14 @@
 
 namespace bcg {
 
-__global__ void k_estar_write(int32_t* e_src, int32_t* e_dst, void* e_w, int32_t* e_len,
-                              int dbytes, EOps ops) {
+__global__ void k_estar_write(int32_t* e_src, void* e_arc, int32_t* e_len, int dbytes, EOps ops) {
     int i = threadIdx.x;
     if (i >= ops.count) return;
     const EOp o = ops.op[i];
     if (o.slot >= 0) {
         e_src[o.slot] = o.a;
-        e_dst[o.slot] = o.b;
-        if (dbytes == 4) static_cast<int32_t*>(e_w)[o.slot] = (int32_t)o.w;
-        else static_cast<int64_t*>(e_w)[o.slot] = o.w;
+        if (dbytes == 4) static_cast<Arc<int32_t>*>(e_arc)[o.slot] = Arc<int32_t>{o.b, (int32_t)o.w};
+        else static_cast<Arc<int64_t>*>(e_arc)[o.slot] = Arc<int64_t>{(int64_t)o.b, o.w};
     }
     atomicMax(e_len + o.a, o.len_a);   // lengths only grow between rebuilds
 }
@@ -253,6 +251,7 @@ struct ScanArgs {
     const uint64_t* cM;    // per column t: multiplier of a tie
     int skip_row;
     int32_t* err;
+    int64_t* stats;        // [4] pairs with a lower distance [5] pairs with new tied paths [6] rows
 };
 
 // The rank-1 rule of Lemma 2 / Lemma 4 for one pair, given the candidate distance
@@ -261,7 +260,7 @@ struct ScanArgs {
 template <typename DT>
 __device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx, uint64_t rs,
                                           uint64_t rm, uint64_t cs, uint64_t cm,
-                                          uint64_t* S, int32_t* err, int64_t* newd) {
+                                          uint64_t* S, int32_t* err, int64_t* newd, int* ties) {
     if (cand == SAT) {
         if (old == Inf<DT>::v) set_err(err, ERRF_DIST);
         return false;
@@ -273,7 +272,10 @@ __device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx,
         return true;
     }
     const uint64_t p = mul_chk(rm, cm, err);
-    if (p != 0ull) S[idx] = add_chk(S[idx], p, err);
+    if (p != 0ull) {
+        S[idx] = add_chk(S[idx], p, err);
+        ++*ties;
+    }
     return false;
 }
 
@@ -283,7 +285,10 @@ __device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx,
 // the pair changes.
 template <typename DT, bool VECTOR>
 __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
-    if (*a.err) return;
+    // warp-uniform early exit: the warp sum at the end needs every lane
+    int bad = 0;
+    if ((threadIdx.x & 31) == 0) bad = *reinterpret_cast<volatile int32_t*>(a.err);
+    if (__shfl_sync(0xffffffffu, bad, 0)) return;
     using V = Vec<DT>;
     constexpr int VN = V::N;
     constexpr int CW = kScanThreads * VN * kScanUnroll;
@@ -291,6 +296,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
     const int nchunks = (n + CW - 1) / CW;
     const int64_t total = (int64_t)(*a.count) * nchunks;
     const int64_t INF = Inf<DT>::v;
+    int n_changed = 0, n_ties = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6),
+                                                       (unsigned long long)(*a.count));
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int i = (int)(item / nchunks);
         const int c = (int)(item - (int64_t)i * nchunks);
@@ -327,9 +335,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
                     const int64_t cand = dsum<DT>(rd, cd[q]);
                     int64_t nd;
                     if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q],
-                                      a.S, a.err, &nd)) {
+                                      a.S, a.err, &nd, &n_ties)) {
                         V::set(dv, q, nd);
                         wr = true;
+                        ++n_changed;
                     }
                 }
                 if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv;
@@ -341,10 +350,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
                 const int64_t old = Drow[t];
                 const int64_t cand = dsum<DT>(rd, cd);
                 int64_t nd;
-                if (pair_rule<DT>(cand, old, rowoff + t, rs, rm, a.cS[t], a.cM[t], a.S, a.err, &nd))
+                if (pair_rule<DT>(cand, old, rowoff + t, rs, rm, a.cS[t], a.cM[t], a.S, a.err, &nd, &n_ties)) {
                     Drow[t] = (DT)nd;
+                    ++n_changed;
+                }
             }
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_changed += __shfl_xor_sync(0xffffffffu, n_changed, o);
+        n_ties += __shfl_xor_sync(0xffffffffu, n_ties, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (n_changed | n_ties)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 4), (unsigned long long)n_changed);
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 5), (unsigned long long)n_ties);
     }
 }
 
@@ -361,12 +381,12 @@ __global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, cons
 // keep[e] = 1 when slot e holds an arc (a,b) with w(a,b) == d(a,b), i.e. an arc of E*
 // (an arc lies on a shortest path exactly when it is one itself).
 template <typename DT>
-__global__ void k_estar_keep(int n, const DT* D, const int32_t* e_src, const int32_t* e_dst,
-                             const DT* e_w, int64_t cap, uint8_t* keep) {
+__global__ void k_estar_keep(int n, const DT* D, const int32_t* e_src, const Arc<DT>* e_arc,
+                             int64_t cap, uint8_t* keep) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= cap) return;
-    const int32_t b = e_dst[e];
-    keep[e] = (b >= 0 && (int64_t)D[(size_t)e_src[e] * n + b] == (int64_t)e_w[e]) ? 1 : 0;
+    const Arc<DT> a = e_arc[e];
+    keep[e] = (a.dst >= 0 && (int64_t)D[(size_t)e_src[e] * n + a.dst] == (int64_t)a.w) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ launches
@@ -375,7 +395,7 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_estar_write(const Dev& d, const EOps& ops) {
     if (ops.count <= 0) return;
-    k_estar_write<<<1, kMaxEOps, 0, d.st>>>(d.e_src, d.e_dst, d.e_w, d.e_len, d.dbytes, ops);
+    k_estar_write<<<1, kMaxEOps, 0, d.st>>>(d.e_src, d.e_arc, d.e_len, d.dbytes, ops);
 }
 
 void launch_alg4_in(const Dev& d, int32_t v, const VEdge* e, int32_t k) {
@@ -440,6 +460,7 @@ static ScanArgs<DT> scan_args(const Dev& d) {
     a.fM = d.fM;
     a.skip_row = -1;
     a.err = d.err;
+    a.stats = d.stats;
     return a;
 }
 
@@ -493,10 +514,10 @@ void launch_estar_keep(const Dev& d, uint8_t* keep) {
     if (d.e_cap <= 0) return;
     if (d.dbytes == 4)
         k_estar_keep<int32_t><<<nblk(d.e_cap, 256), 256, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.e_src, d.e_dst, (const int32_t*)d.e_w, d.e_cap, keep);
+            d.n, (const int32_t*)d.D, d.e_src, (const Arc<int32_t>*)d.e_arc, d.e_cap, keep);
     else
         k_estar_keep<int64_t><<<nblk(d.e_cap, 256), 256, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.e_src, d.e_dst, (const int64_t*)d.e_w, d.e_cap, keep);
+            d.n, (const int64_t*)d.D, d.e_src, (const Arc<int64_t>*)d.e_arc, d.e_cap, keep);
 }
 
 }  // namespace bcg
