@@ -231,6 +231,35 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
  */
 int bc_set_option(bc_graph* g, const char* name, int64_t value);
 
+/*
+ * bc_static_scores_noalloc -- BC(v) of a small graph that is already in device memory,
+ * computed without allocating any device memory.  (The paper has no counterpart: this
+ * serves callers that cannot call cudaMalloc -- a process whose device memory belongs to
+ * a framework's caching allocator, or a serving runtime that reserves HBM at start-up
+ * and allows no later allocation, cudaMalloc being able to synchronise the device.)
+ * It runs the static computation of bc_init_static with every arc as the E* superset
+ * and keeps all scratch in one fixed array inside the library (about 12 MB, held on
+ * every GPU that loads the library until the process exits).
+ *   n            vertices, 1 .. 512; larger graphs are rejected with BC_ERR_ARG.
+ *   arcs         arcs in d_dst / d_w, 0 .. 32768 (BC_ERR_ARG beyond).
+ *   d_off        DEVICE int32[n+1]: CSR offsets by tail (arcs of a in [d_off[a], d_off[a+1])).
+ *   d_dst, d_w   DEVICE int32 / int64 [arcs]: head and weight of each arc, weight in
+ *                [1, INF-1] of the distance type.  An undirected graph is passed as
+ *                G_D (both arcs of every edge).  The graph must be simple; a bad
+ *                endpoint or weight found on the device returns BC_ERR_ARG.
+ *   flags        as for bc_init_static.
+ *   d_scores     DEVICE double[n]: receives BC (halved G_D sums for undirected).
+ *   cuda_stream  stream for all the work (NULL = legacy default stream).
+ * Synchronous.  Calls no cudaMalloc / cudaFree and no allocating library routine.
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the one scratch array, which keeps the previous
+ * call's contents (the call clears what must start at zero); calls whose work overlaps
+ * on the GPU -- from several host threads or on several streams -- race on it.
+ */
+int bc_static_scores_noalloc(int32_t n, int64_t arcs, const int32_t* d_off, const int32_t* d_dst,
+                             const int64_t* d_w, uint32_t flags, double* d_scores, void* cuda_stream);
+
 /* bc_destroy -- free the handle and its device memory (waits for its stream). */
 void bc_destroy(bc_graph* g);
 

@@ -39,7 +39,8 @@ INF64 = np.iinfo(np.int64).max
 
 EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "bc_apply_updates",
            "bc_stage_updates", "bc_run_staged", "bc_synchronize", "bc_query", "bc_get_scores",
-           "bc_get_rows", "bc_get_info", "bc_get_profile", "bc_set_option", "bc_destroy", "bc_last_error"]
+           "bc_get_rows", "bc_get_info", "bc_get_profile", "bc_set_option", "bc_destroy", "bc_last_error",
+           "bc_static_scores_noalloc"]
 PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping"]
 
 
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = True):
         "bc_set_option": ([p, ctypes.c_char_p, i64], ctypes.c_int),
         "bc_destroy": ([p], None),
         "bc_last_error": ([p], ctypes.c_char_p),
+        "bc_static_scores_noalloc": ([i32, i64, p, p, p, u32, p, p], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -25,7 +25,7 @@
 
 namespace bcg {
 
-enum : int32_t { ERRF_OVERFLOW = 1, ERRF_DIST = 2, ERRF_TIMEOUT = 4 };
+enum : int32_t { ERRF_OVERFLOW = 1, ERRF_DIST = 2, ERRF_TIMEOUT = 4, ERRF_ARG_DEVICE = 8 };
 
 // Saturation marker for a distance sum that does not fit: INT64_MAX.  For DT =
 // int64 this equals INF, so callers test for it before comparing.
