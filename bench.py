@@ -361,6 +361,32 @@ def run_ours(args):
     return 0
 
 
+def run_ncu_case(args):
+    """A small case of one kernel class for ncu captures (a few GB on the device at most):
+    BA n=8192 (state 1.3 GB, above L2), static init, then either two vertex updates
+    (accumulation and BC rows) or one edge update with the rank-1 pass over every row
+    (the paper's all-pairs Step 2)."""
+    from paper_1311_2147_gb300 import binding, synth
+    binding.load()
+    g, ups = synth.workload_ba16384(n=args.ncu_n, n_updates=64)
+    bg = binding.BCGraph(g, dist="i32")
+    if args.ncu_case == "scan":
+        bg.bc_set_option("full_scan", 1)
+        sel = [u for u in ups if u[0] == "edge"][:2]
+    else:
+        sel = [u for u in ups if u[0] == "vertex"][:2]
+    per_update = []
+    for u in sel:
+        before = bg.bc_get_info()
+        rc, _ = bg.bc_apply_updates([u])
+        assert rc == 0, bg.last_error()
+        after = bg.bc_get_info()
+        per_update.append({k: after[k] - before[k] for k in ("rows_reaccumulated", "rows_scanned",
+                                                             "pairs_lowered", "pairs_tied")})
+    print(json.dumps({"ncu_case": args.ncu_case, "n": g.n, "per_update": per_update, "info": bg.bc_get_info()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,7 +399,12 @@ def main():
     ap.add_argument("--recompute-runs", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--ncu-case", choices=["accumulate", "scan"], default=None,
+                    help="run only a small case of one kernel class (for ncu captures)")
+    ap.add_argument("--ncu-n", type=int, default=8192)
     args = ap.parse_args()
+    if args.ncu_case:
+        return run_ncu_case(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

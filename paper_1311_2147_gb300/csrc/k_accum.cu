@@ -114,45 +114,15 @@ __device__ __forceinline__ void finish_vertex(int x, ff acc, uint64_t sigma, ff*
 
 // Passes 2 and 3 walk only the arcs of DAG'(s): pass 1 evaluates the predicate once per
 // slot of the E* superset and records it in a bit mask (one warp ballot per 32 slots).
-// A vertex is then handled by one thread, over the set bits of its slot range, unless
-// it has more than kBigDag DAG out-arcs: such vertices go to a short list that whole
-// warps take after the threads (lanes over the slots, fixed butterfly).
-constexpr int kBigDag = 16;
+// Within a level, the DAG arcs of the level's vertices are spread evenly over the
+// threads: a block scan of the vertices' DAG out-degrees gives each arc a rank, a
+// thread finds the owner of its rank by binary search and the arc by selecting the
+// right set bit of the owner's slot range.  In pass 3 the arcs' contributions go to a
+// shared buffer and each owner adds its own in rank order (deterministic).  Vertices
+// with more than kBigDag DAG out-arcs are taken by whole warps instead (lanes over
+// their slots, fixed butterfly), so no owner loops long.
+constexpr int kBigDag = 32;
 constexpr int kBigCap = 2048;
-
-// Iterator over the set bits of mask within the slot range [beg, end).
-struct BitCursor {
-    const uint32_t* mask;
-    int word, last;
-    uint32_t bits;
-    __device__ __forceinline__ void init(const uint32_t* m, int beg, int end) {
-        mask = m;
-        if (beg >= end) {
-            word = 1;
-            last = 0;
-            bits = 0;
-            return;
-        }
-        word = beg >> 5;
-        last = (end - 1) >> 5;
-        bits = m[word] & (0xffffffffu << (beg & 31));
-        if (word == last) bits &= 0xffffffffu >> (31 - ((end - 1) & 31));
-        endbit = end;
-    }
-    int endbit;
-    // next set slot, or -1
-    __device__ __forceinline__ int next() {
-        while (bits == 0) {
-            if (word >= last) return -1;
-            ++word;
-            bits = mask[word];
-            if (word == last) bits &= 0xffffffffu >> (31 - ((endbit - 1) & 31));
-        }
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        return (word << 5) + b;
-    }
-};
 
 __device__ __forceinline__ int count_bits(const uint32_t* m, int beg, int end) {
     if (beg >= end) return 0;
@@ -165,6 +135,62 @@ __device__ __forceinline__ int count_bits(const uint32_t* m, int beg, int end) {
         c += __popc(b);
     }
     return c;
+}
+
+// Slot of the r-th (0-based) set bit of m within [beg, end); the bit exists.
+__device__ __forceinline__ int select_bit(const uint32_t* m, int beg, int end, int r) {
+    const int w1 = (end - 1) >> 5;
+    int w = beg >> 5;
+    uint32_t b = m[w] & (0xffffffffu << (beg & 31));
+    for (;;) {
+        if (w == w1) b &= 0xffffffffu >> (31 - ((end - 1) & 31));
+        const int c = __popc(b);
+        if (r < c) break;
+        r -= c;
+        b = m[++w];
+    }
+    for (; r > 0; --r) b &= b - 1u;
+    return (w << 5) + __ffs(b) - 1;
+}
+
+// Exclusive block-wide prefix sum of v (all threads call it); *total gets the sum.
+// s_ws needs kAccThreads / 32 + 1 ints and must not be reused before a barrier.
+__device__ __forceinline__ int block_excl_scan(int v, int* s_ws, int* total) {
+    constexpr int NW = kAccThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < NW ? s_ws[lane] : 0;
+        int ix = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, ix, o);
+            if (lane >= o) ix += y;
+        }
+        if (lane < NW) s_ws[lane] = ix - x;
+        if (lane == NW - 1) s_ws[NW] = ix;
+    }
+    __syncthreads();
+    *total = s_ws[NW];
+    return s_ws[warp] + incl - v;
+}
+
+// Last index i in [0, kAccThreads) with off[i] <= j (off non-decreasing, off[0] = 0).
+__device__ __forceinline__ int owner_of(const int* off, int j) {
+    int lo = 0, hi = kAccThreads;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Append x to the big list when there is room (warp-aggregated); returns whether it was.
@@ -192,29 +218,53 @@ __device__ __forceinline__ void push_sigma(uint64_t* Ss, int b, uint64_t sx, int
     }
 }
 
+// Per-round shared scratch of the level passes.
+struct LevelSmem {
+    int off[kAccThreads];
+    int beg[kAccThreads];
+    int end[kAccThreads];
+    uint64_t sx[kAccThreads];
+    ff buf[kAccThreads];
+    int ws[kAccThreads / 32 + 1];
+};
+
 template <typename DT, bool STATIC, typename DA>
 __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA dist, int s, uint64_t* Ss,
                                                   ff* out, uint32_t* cnt, uint16_t* order, uint32_t* mask,
-                                                  uint16_t* big, ff* rho, int32_t* lvl, int* s_tail, int* s_nbig) {
+                                                  uint16_t* big, LevelSmem& ls, ff* rho, int32_t* lvl,
+                                                  int* s_tail, int* s_nbig) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int T = kAccThreads, NW = kAccThreads / 32;
-    // ---- pass 1: DAG'(s) membership of every slot, and in-degrees
+    constexpr int T = kAccThreads, NW = kAccThreads / 32, U = 4;
+    // ---- pass 1: DAG'(s) membership of every slot, and in-degrees (loads of U chunks
+    // are issued before any of them is used)
     const int nchunk = (int)((a.e_cap + 31) >> 5);
-    for (int c = warp; c < nchunk; c += NW) {
-        const int64_t e = ((int64_t)c << 5) + lane;
-        bool on = false;
-        int b = 0;
-        if (e < a.e_cap) {
-            const Arc<DT> r = a.e_arc[e];
-            b = (int)r.dst;
-            if (b >= 0) {
-                const uint64_t dx = dist(a.e_src[e]);
-                on = dx != DA::INFV && on_dag(dist, dx, b, (uint64_t)r.w);
+    for (int c0 = warp; c0 < nchunk; c0 += U * NW) {
+        Arc<DT> r[U];
+        int src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = ((int64_t)(c0 + u * NW) << 5) + lane;
+            r[u].dst = -1;
+            src[u] = 0;
+            if (e < a.e_cap) {
+                r[u] = a.e_arc[e];
+                src[u] = a.e_src[e];
             }
         }
-        if (on) cnt_inc(cnt, b);
-        const unsigned word = __ballot_sync(FULL, on);
-        if (lane == 0) mask[c] = word;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + u * NW;
+            if (c >= nchunk) break;
+            const int b = (int)r[u].dst;
+            bool on = false;
+            if (b >= 0) {
+                const uint64_t dx = dist(src[u]);
+                on = dx != DA::INFV && on_dag(dist, dx, b, (uint64_t)r[u].w);
+            }
+            if (on) cnt_inc(cnt, b);
+            const unsigned word = __ballot_sync(FULL, on);
+            if (lane == 0) mask[c] = word;
+        }
     }
     __syncthreads();   // the distance row (aliased by order) is dead from here on
     if (tid == 0) {
@@ -239,24 +289,28 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                 k = count_bits(mask, beg, end);
             }
             if (big_push(k > kBigDag, x, big, s_nbig)) k = 0;
-            uint64_t sx = 0;
-            if (STATIC && k) sx = Ss[x];
-            BitCursor cur;
-            cur.init(mask, beg, k ? end : beg);
-            const int iters = __reduce_max_sync(FULL, k);
-            for (int it = 0; it < iters; ++it) {
+            int total;
+            const int off = block_excl_scan(k, ls.ws, &total);
+            ls.off[tid] = off;
+            ls.beg[tid] = beg;
+            ls.end[tid] = end;
+            if (STATIC) ls.sx[tid] = k ? Ss[x] : 0ull;
+            __syncthreads();
+            for (int jb = 0; jb < total; jb += T) {
+                const int j = jb + tid;
                 bool ready = false;
                 int b = 0;
-                if (it < k) {
-                    const int e = cur.next();
+                if (j < total) {
+                    const int o = owner_of(ls.off, j);
+                    const int e = select_bit(mask, ls.beg[o], ls.end[o], j - ls.off[o]);
                     b = (int)a.e_arc[e].dst;
-                    push_sigma<DT, STATIC>(Ss, b, sx, a.err);
+                    push_sigma<DT, STATIC>(Ss, b, STATIC ? ls.sx[o] : 0ull, a.err);
                     ready = cnt_last(cnt, b);
                 }
                 warp_append(ready, b, order, s_tail);
             }
+            __syncthreads();
         }
-        __syncthreads();
         const int nb = min(*s_nbig, kBigCap);
         for (int i = warp; i < nb; i += NW) {
             const int x = big[i];
@@ -296,14 +350,29 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                 k = count_bits(mask, beg, end);
             }
             const bool is_big = big_push(k > kBigDag, x, big, s_nbig);
-            if (q < hi && !is_big) {
-                const uint64_t sig = Ss[x];
-                BitCursor cur;
-                cur.init(mask, beg, end);
-                ff acc{0.0f, 0.0f};
-                for (int e = cur.next(); e >= 0; e = cur.next()) acc = ff_add(acc, rho[a.e_arc[e].dst]);
-                finish_vertex(x, acc, sig, out, rho);
+            if (is_big) k = 0;
+            const bool mine = q < hi && !is_big;
+            const uint64_t sig = mine ? Ss[x] : 1ull;
+            int total;
+            const int off = block_excl_scan(k, ls.ws, &total);
+            ls.off[tid] = off;
+            ls.beg[tid] = beg;
+            ls.end[tid] = end;
+            __syncthreads();
+            ff acc{0.0f, 0.0f};
+            for (int jb = 0; jb < total; jb += T) {
+                const int j = jb + tid;
+                if (j < total) {
+                    const int o = owner_of(ls.off, j);
+                    const int e = select_bit(mask, ls.beg[o], ls.end[o], j - ls.off[o]);
+                    ls.buf[tid] = rho[a.e_arc[e].dst];
+                }
+                __syncthreads();
+                const int p0 = max(off, jb), p1 = min(off + k, jb + T);
+                for (int p = p0; p < p1; ++p) acc = ff_add(acc, ls.buf[p - jb]);
+                __syncthreads();
             }
+            if (mine) finish_vertex(x, acc, sig, out, rho);
         }
         __syncthreads();
         const int nb = min(*s_nbig, kBigCap);
@@ -324,10 +393,12 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
 
 // One CTA per source at a time.  Shared memory: [d16 | order] (the distance row is dead
 // once the slot mask is built, so the level order reuses it) | cnt (n/2 words) |
-// big list | slot mask (here when it fits, else in the work space).
+// big list | slot mask (here when it fits, else in the work space); the per-round
+// scratch of the level passes is static shared memory.
 template <typename DT, bool STATIC>
 __global__ void __launch_bounds__(kAccThreads) k_accum_smem(AccArgs<DT> a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LevelSmem ls;
     const int n = a.n;
     const int np = (n + 31) & ~31;
     uint16_t* d16 = reinterpret_cast<uint16_t*>(smem);
@@ -363,10 +434,11 @@ __global__ void __launch_bounds__(kAccThreads) k_accum_smem(AccArgs<DT> a) {
         for (int t = tid; t < np / 2; t += kAccThreads) cnt[t] = 0u;
         wide = __syncthreads_or(wide);
         if (!wide)
-            accumulate_source<DT, STATIC>(a, Dist16{d16}, s, Ss, out, cnt, order, mask, big, rho, lvl, &s_tail, &s_nbig);
-        else
-            accumulate_source<DT, STATIC>(a, DistG<DT>{Ds}, s, Ss, out, cnt, order, mask, big, rho, lvl, &s_tail,
+            accumulate_source<DT, STATIC>(a, Dist16{d16}, s, Ss, out, cnt, order, mask, big, ls, rho, lvl, &s_tail,
                                           &s_nbig);
+        else
+            accumulate_source<DT, STATIC>(a, DistG<DT>{Ds}, s, Ss, out, cnt, order, mask, big, ls, rho, lvl,
+                                          &s_tail, &s_nbig);
         __syncthreads();
     }
 }

@@ -234,7 +234,7 @@ template <> struct Vec<int64_t> {
 };
 
 constexpr int kScanThreads = 256;
-constexpr int kScanUnroll = 2;
+constexpr int kScanUnroll = 4;
 
 template <typename DT>
 struct ScanArgs {
@@ -280,11 +280,12 @@ __device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx,
 }
 
 // K2: in-place rank-1 min-plus / path-count pass over rows[0..count) x all columns.
-// Work item = (row, column chunk); a persistent grid walks the items.  Distances are
-// read with 16-byte vector loads; sigma is read only on ties and written only where
-// the pair changes.
+// Work item = (row, chunk of CW columns).  Each CTA takes a contiguous block of items,
+// so the per-row scalars are loaded once per row it meets; each thread issues all of
+// its 16-byte loads of D and of the column vectors of an item before using any.  sigma
+// is read only on ties and written only where the pair changes.
 template <typename DT, bool VECTOR>
-__global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
     // warp-uniform early exit: the warp sum at the end needs every lane
     int bad = 0;
     if ((threadIdx.x & 31) == 0) bad = *reinterpret_cast<volatile int32_t*>(a.err);
@@ -295,39 +296,72 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
     const int n = a.n;
     const int nchunks = (n + CW - 1) / CW;
     const int64_t total = (int64_t)(*a.count) * nchunks;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t it0 = (int64_t)blockIdx.x * per;
+    const int64_t it1 = min(total, it0 + per);
     const int64_t INF = Inf<DT>::v;
     int n_changed = 0, n_ties = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6),
                                                        (unsigned long long)(*a.count));
-    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    int cur = -1, s = -1;
+    int64_t rd = INF;
+    uint64_t rs = 0, rm = 0;
+    for (int64_t item = it0; item < it1; ++item) {
         const int i = (int)(item / nchunks);
         const int c = (int)(item - (int64_t)i * nchunks);
-        const int s = a.rows[i];
-        if (s == a.skip_row) continue;
-        const int64_t rd = a.fD[s];
+        if (i != cur) {
+            cur = i;
+            s = a.rows[i];
+            rd = (s == a.skip_row) ? INF : (int64_t)a.fD[s];
+            rs = a.fS[s];
+            rm = a.fM[s];
+        }
         if (rd == INF) continue;
-        const uint64_t rs = a.fS[s], rm = a.fM[s];
         const size_t rowoff = (size_t)s * n;
         DT* __restrict__ Drow = a.D + rowoff;
         const int t0 = c * CW;
         if constexpr (VECTOR) {
+            typename V::T dv[kScanUnroll], cv[kScanUnroll];
+#pragma unroll
+            for (int u = 0; u < kScanUnroll; ++u) {
+                const int t = t0 + (u * kScanThreads + threadIdx.x) * VN;
+                if (t < n) {
+                    dv[u] = __ldcs(reinterpret_cast<const typename V::T*>(Drow + t));
+                    cv[u] = __ldg(reinterpret_cast<const typename V::T*>(a.cD + t));
+                }
+            }
 #pragma unroll
             for (int u = 0; u < kScanUnroll; ++u) {
                 const int t = t0 + (u * kScanThreads + threadIdx.x) * VN;
                 if (t >= n) break;
-                typename V::T dv = *reinterpret_cast<const typename V::T*>(Drow + t);
-                const typename V::T cv = __ldg(reinterpret_cast<const typename V::T*>(a.cD + t));
-                int64_t dd[VN], cd[VN];
-                V::unpack(dv, dd);
-                V::unpack(cv, cd);
                 bool any = false;
+                if constexpr (sizeof(DT) == 4) {
+                    // both terms are below 2^31, so their sum fits 32 bits: a pair can change
+                    // only if the column term is finite and the sum does not exceed d (or d
+                    // is INF, where a sum that does not fit must be reported)
+                    const uint32_t r32 = (uint32_t)rd;
+                    const int32_t* dp = reinterpret_cast<const int32_t*>(&dv[u]);
+                    const int32_t* cp = reinterpret_cast<const int32_t*>(&cv[u]);
 #pragma unroll
-                for (int q = 0; q < VN; ++q) {
-                    if (cd[q] == INF) continue;
-                    const int64_t cand = dsum<DT>(rd, cd[q]);
-                    any |= (cand <= dd[q]) || (cand == SAT);
+                    for (int q = 0; q < VN; ++q) {
+                        const uint32_t sum = r32 + (uint32_t)cp[q];
+                        any |= (cp[q] != INT32_MAX) & ((sum <= (uint32_t)dp[q]) | (dp[q] == INT32_MAX));
+                    }
+                } else {
+                    int64_t dd0[VN], cd0[VN];
+                    V::unpack(dv[u], dd0);
+                    V::unpack(cv[u], cd0);
+#pragma unroll
+                    for (int q = 0; q < VN; ++q) {
+                        if (cd0[q] == INF) continue;
+                        const int64_t cand = dsum<DT>(rd, cd0[q]);
+                        any |= (cand <= dd0[q]) || (cand == SAT);
+                    }
                 }
                 if (!any) continue;
+                int64_t dd[VN], cd[VN];
+                V::unpack(dv[u], dd);
+                V::unpack(cv[u], cd);
                 bool wr = false;
 #pragma unroll
                 for (int q = 0; q < VN; ++q) {
@@ -336,12 +370,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs<DT> a) {
                     int64_t nd;
                     if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q],
                                       a.S, a.err, &nd, &n_ties)) {
-                        V::set(dv, q, nd);
+                        V::set(dv[u], q, nd);
                         wr = true;
                         ++n_changed;
                     }
                 }
-                if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv;
+                if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv[u];
             }
         } else {
             for (int t = t0 + threadIdx.x; t < t0 + CW && t < n; t += kScanThreads) {
