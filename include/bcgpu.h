@@ -260,6 +260,47 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value);
 int bc_static_scores_noalloc(int32_t n, int64_t arcs, const int32_t* d_off, const int32_t* d_dst,
                              const int64_t* d_w, uint32_t flags, double* d_scores, void* cuda_stream);
 
+/*
+ * Batches: many graphs updated together.  Round r applies the r-th update of every graph
+ * that has one; within a round each phase of the update (Algorithm 4 and Lemma 2 / 4 in
+ * both directions, DAG rebuild, Kahn order, Eq. 4, BC) runs as one kernel over the work
+ * of all graphs at once, and the rounds are captured once into a CUDA graph that is
+ * replayed by one graph launch per call.  A graph's result is bit-identical to applying
+ * the same updates to it alone.  The graphs must share the distance type; they stay
+ * owned by the caller and must not be used by other calls while a batch call runs.
+ */
+typedef struct bc_batch bc_batch;
+
+/* bc_batch_create -- group count handles (host array of handles) on a CUDA stream
+ * (NULL: the batch creates its own, since the legacy default stream cannot be captured
+ * into a CUDA graph).  BC_ERR_ARG for a NULL or poisoned handle or mixed distance types. */
+int bc_batch_create(bc_batch** out, int32_t count, bc_graph* const* graphs, void* cuda_stream);
+
+/*
+ * bc_batch_apply -- n_updates[g] updates for graph g, concatenated in graph order in
+ * ups (host arrays); vertex updates index edges as in bc_apply_updates.  Each graph's
+ * updates are validated in order; a graph stops at its first invalid update (the updates
+ * before it are applied) and the first such status is returned.  n_done (optional, G
+ * entries) receives how many updates each graph applied.  Synchronous; device-side
+ * errors poison only the graphs they occur in.
+ */
+int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, const bc_vedge* edges,
+                   int64_t n_edges, int32_t* n_done);
+
+/* bc_batch_set_tiles -- launch shape of the batch kernels (what the autotuner varies):
+ * tiles[0] CTAs per SM of the per-vertex passes (1..64), tiles[1] of the rank-1 pass,
+ * tiles[2] of the BC row sums, tiles[3] cap on accumulation CTAs per SM (0 = as many as
+ * fit).  The next bc_batch_apply captures a new CUDA graph. */
+int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count);
+
+/* bc_batch_last_ms -- device time (CUDA events around the graph launch) of the last apply. */
+int bc_batch_last_ms(bc_batch* b, double* ms);
+
+const char* bc_batch_last_error(const bc_batch* b);
+
+/* bc_batch_destroy -- free the batch (not the graphs). */
+void bc_batch_destroy(bc_batch* b);
+
 /* bc_destroy -- free the handle and its device memory (waits for its stream). */
 void bc_destroy(bc_graph* g);
 

@@ -40,7 +40,8 @@ INF64 = np.iinfo(np.int64).max
 EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "bc_apply_updates",
            "bc_stage_updates", "bc_run_staged", "bc_synchronize", "bc_query", "bc_get_scores",
            "bc_get_rows", "bc_get_info", "bc_get_profile", "bc_set_option", "bc_destroy", "bc_last_error",
-           "bc_static_scores_noalloc"]
+           "bc_static_scores_noalloc", "bc_batch_create", "bc_batch_apply", "bc_batch_set_tiles",
+           "bc_batch_last_ms", "bc_batch_last_error", "bc_batch_destroy"]
 PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping"]
 
 
@@ -96,6 +97,12 @@ def load(build_if_missing: bool = True):
         "bc_destroy": ([p], None),
         "bc_last_error": ([p], ctypes.c_char_p),
         "bc_static_scores_noalloc": ([i32, i64, p, p, p, u32, p, p], ctypes.c_int),
+        "bc_batch_create": ([ctypes.POINTER(p), i32, p, p], ctypes.c_int),
+        "bc_batch_apply": ([p, p, p, p, i64, p], ctypes.c_int),
+        "bc_batch_set_tiles": ([p, p, i32], ctypes.c_int),
+        "bc_batch_last_ms": ([p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bc_batch_last_error": ([p], ctypes.c_char_p),
+        "bc_batch_destroy": ([p], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -230,3 +237,53 @@ class BCGraph:
 
     def last_error(self):
         return self.lib.bc_last_error(self.h).decode()
+
+
+class BCBatch:
+    """A batch of device-resident graphs updated together (one CUDA graph launch per call)."""
+
+    def __init__(self, graphs, stream=None):
+        self.lib = load()
+        self.graphs = list(graphs)
+        hs = (ctypes.c_void_p * len(self.graphs))(*[g.h.value for g in self.graphs])
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = self.lib.bc_batch_create(ctypes.byref(h), len(self.graphs), ctypes.cast(hs, ctypes.c_void_p), st)
+        if rc != BC_OK:
+            raise BCError(rc, "bc_batch_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bc_batch_apply(self, per_graph_updates):
+        """per_graph_updates: one list of update tuples per graph.  Returns (rc, n_done)."""
+        counts = np.array([len(u) for u in per_graph_updates], dtype=np.int32)
+        flat = [u for us in per_graph_updates for u in us]
+        rec, ed = encode_updates(flat)
+        done = np.zeros(len(self.graphs), dtype=np.int32)
+        rc = self.lib.bc_batch_apply(self.h, _ptr(counts), _ptr(rec) if rec.size else None,
+                                     _ptr(ed) if ed.size else None, int(ed.shape[0]), _ptr(done))
+        return rc, done
+
+    def bc_batch_set_tiles(self, tiles):
+        t = np.ascontiguousarray(tiles, dtype=np.int32)
+        rc = self.lib.bc_batch_set_tiles(self.h, _ptr(t), int(t.shape[0]))
+        if rc != BC_OK:
+            raise BCError(rc, self.last_error())
+
+    def bc_batch_last_ms(self):
+        ms = ctypes.c_double(0.0)
+        self.lib.bc_batch_last_ms(self.h, ctypes.byref(ms))
+        return ms.value
+
+    def last_error(self):
+        return self.lib.bc_batch_last_error(self.h).decode()

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bcgpu.h"
+#include "bc_batch.cuh"
 #include "bc_internal.cuh"
 
 using namespace bcg;
@@ -180,13 +181,14 @@ int sync_check(bc_graph* g) {
 }
 
 // Lay the E* superset out with slack per vertex and upload it.
-int estar_layout(bc_graph* g, const std::vector<HArc>& arcs) {
+int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<int32_t>* extra = nullptr) {
     const int32_t n = g->n;
     std::vector<int32_t> deg(n, 0);
     for (const HArc& x : arcs) deg[x.a]++;
     g->e_off.assign(n + 1, 0);
     g->e_len.assign(n, 0);
-    for (int32_t a = 0; a < n; ++a) g->e_off[a + 1] = g->e_off[a] + deg[a] + 2 + deg[a] / 8;
+    for (int32_t a = 0; a < n; ++a)
+        g->e_off[a + 1] = g->e_off[a] + deg[a] + 2 + deg[a] / 8 + (extra ? (*extra)[a] : 0);
     const int64_t cap = g->e_off[n];
     g->e_src.assign(cap, 0);
     g->e_dst.assign(cap, -1);
@@ -840,6 +842,384 @@ void bc_destroy(bc_graph* g) { destroy_all(g); }
 
 const char* bc_last_error(const bc_graph* g) {
     return g ? g->last_error.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+
+struct bc_batch {
+    std::vector<bc_graph*> graphs;
+    int32_t G = 0;
+    int dbytes = 4;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;   // the legacy default stream cannot be captured
+    BatchLaunch L{};
+    BatchArgs args{};
+    int32_t n_max = 0;
+    int64_t cap_max = 0;
+    // device buffers (fixed while a captured graph refers to them)
+    Dev* d_devs = nullptr;
+    BatchUpd* d_upd = nullptr;
+    VEdge* d_entries = nullptr;
+    BatchEOp* d_eops = nullptr;
+    int64_t* d_eop_off = nullptr;
+    int64_t* d_voff = nullptr;
+    int64_t* d_coff = nullptr;
+    int64_t* d_plans = nullptr;
+    int32_t* d_ws = nullptr;
+    int64_t R_cap = 0, E_cap = 0, O_cap = 0, ws_cap = 0;
+    cudaGraphExec_t exec = nullptr;
+    int32_t exec_rounds = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double last_ms = 0.0;
+    std::string last_error;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int bfail(bc_batch* b, int code, const std::string& msg) {
+    if (b) b->last_error = msg;
+    return code;
+}
+
+#define CKB(b, call)                                                                           \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA,        \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+template <typename T>
+int balloc(bc_batch* b, T** p, size_t count) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return bfail(b, BC_ERR_OOM, "cudaMalloc failed for a batch buffer");
+    b->allocs.push_back(*p);
+    return BC_OK;
+}
+
+void bfree(bc_batch* b, void* p) {
+    if (!p) return;
+    auto it = std::find(b->allocs.begin(), b->allocs.end(), p);
+    if (it != b->allocs.end()) b->allocs.erase(it);
+    cudaFree(p);
+}
+
+void drop_exec(bc_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->exec_rounds = -1;
+}
+
+// Arcs the update would add to the E* superset (not yet in it).
+void new_arcs_of(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::vector<int32_t>& need) {
+    for (const VEdge& e : ent) {
+        auto add = [&](int32_t a, int32_t bb) {
+            if (!g->eslot.count(arc_key(a, bb))) need[a]++;
+        };
+        if (!g->directed) {
+            add(e.x, v);
+            add(v, e.x);
+        } else if (e.dir == 0) {
+            add(e.x, v);
+        } else {
+            add(v, e.x);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int bc_batch_create(bc_batch** out, int32_t count, bc_graph* const* graphs, void* cuda_stream) {
+    if (!out || count < 1 || !graphs) return BC_ERR_ARG;
+    *out = nullptr;
+    bc_batch* b = new bc_batch();
+    b->G = count;
+    b->st = (cudaStream_t)cuda_stream;
+    if (!b->st) {
+        if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return BC_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    b->graphs.assign(graphs, graphs + count);
+    for (int32_t i = 0; i < count; ++i) {
+        bc_graph* g = graphs[i];
+        if (!g || g->poisoned || g->dbytes != graphs[0]->dbytes) {
+            if (b->own_stream) cudaStreamDestroy(b->st);
+            delete b;
+            return BC_ERR_ARG;
+        }
+        b->n_max = std::max(b->n_max, g->n);
+    }
+    b->dbytes = graphs[0]->dbytes;
+    b->L.nsm = graphs[0]->d.nsm;
+    b->L.vpass_ctas = 4;
+    b->L.scan_ctas = 8;
+    b->L.bc_ctas = 8;
+    b->L.acc_per_sm = 0;
+    int rc;
+    if ((rc = balloc(b, &b->d_devs, count)) || (rc = balloc(b, &b->d_coff, count + 1)) ||
+        (rc = balloc(b, &b->d_plans, 3 * ((size_t)count + 1)))) {
+        bc_batch_destroy(b);
+        return rc;
+    }
+    cudaEventCreate(&b->e0);
+    cudaEventCreate(&b->e1);
+    std::vector<int64_t> coff(count + 1, 0);
+    for (int32_t i = 0; i < count; ++i) coff[i + 1] = coff[i] + graphs[i]->n;
+    if (cudaMemcpy(b->d_coff, coff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+        bc_batch_destroy(b);
+        return BC_ERR_CUDA;
+    }
+    *out = b;
+    return BC_OK;
+}
+
+int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count) {
+    if (!b || !tiles || count < 4) return BC_ERR_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (tiles[i] < 0 || tiles[i] > 64) return bfail(b, BC_ERR_ARG, "tile value out of range");
+    if (tiles[0] < 1 || tiles[1] < 1 || tiles[2] < 1) return bfail(b, BC_ERR_ARG, "tile value out of range");
+    b->L.vpass_ctas = tiles[0];
+    b->L.scan_ctas = tiles[1];
+    b->L.bc_ctas = tiles[2];
+    b->L.acc_per_sm = tiles[3];
+    b->cap_max = -1;   // forces a new launch configuration
+    drop_exec(b);
+    return BC_OK;
+}
+
+int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, const bc_vedge* edges,
+                   int64_t n_edges, int32_t* n_done) {
+    if (!b || !n_updates || (!ups && n_edges > 0)) return BC_ERR_ARG;
+    const int32_t G = b->G;
+    int64_t first = 0;
+    int32_t R = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        if (n_updates[g] < 0) return bfail(b, BC_ERR_ARG, "negative update count");
+        R = std::max(R, n_updates[g]);
+        if (n_done) n_done[g] = 0;
+    }
+    for (bc_graph* g : b->graphs) {
+        if (g->poisoned) return bfail(b, BC_ERR_POISONED, "a graph of the batch is poisoned");
+        CKB(b, cudaStreamSynchronize(g->d.st));
+    }
+    int status = BC_OK;
+    // ---- validate each graph's updates in order, size the slack, mirror them
+    std::vector<std::vector<int32_t>> vtx(G);
+    std::vector<std::vector<std::vector<VEdge>>> ents(G);
+    std::vector<int32_t> ok(G, 0);
+    int64_t base = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        bc_graph* gr = b->graphs[g];
+        // validation reads the host weights as they evolve: validate on a copy of the
+        // weights first, then mirror for real once the slack is known to suffice
+        std::unordered_map<uint64_t, int64_t> saved = gr->wmap;
+        std::vector<int32_t> need(gr->n, 0);
+        std::vector<VEdge> ent;
+        for (int32_t k = 0; k < n_updates[g]; ++k) {
+            const bc_update& u = ups[base + k];
+            int32_t v = -1;
+            int rc = validate_update(gr, u, edges, n_edges, &v, ent);
+            if (rc) {
+                if (status == BC_OK) status = rc;
+                b->last_error = gr->last_error;
+                break;
+            }
+            new_arcs_of(gr, v, ent, need);
+            for (const VEdge& e : ent) {   // tentative weights so later updates validate against them
+                if (!gr->directed) {
+                    gr->wmap[arc_key(e.x, v)] = e.w;
+                    gr->wmap[arc_key(v, e.x)] = e.w;
+                } else if (e.dir == 0) {
+                    gr->wmap[arc_key(e.x, v)] = e.w;
+                } else {
+                    gr->wmap[arc_key(v, e.x)] = e.w;
+                }
+            }
+            vtx[g].push_back(v);
+            ents[g].push_back(ent);
+            ok[g]++;
+        }
+        gr->wmap.swap(saved);
+        base += n_updates[g];
+        bool short_slack = false;
+        for (int32_t a = 0; a < gr->n && !short_slack; ++a)
+            if (need[a] > gr->e_off[a + 1] - gr->e_off[a] - gr->e_len[a]) short_slack = true;
+        if (short_slack) {
+            std::vector<HArc> arcs;
+            for (size_t s2 = 0; s2 < gr->e_dst.size(); ++s2)
+                if (gr->e_dst[s2] >= 0) arcs.push_back({gr->e_src[s2], gr->e_dst[s2], gr->e_w[s2]});
+            int rc = estar_layout(gr, arcs, &need);
+            if (rc) return bfail(b, rc, gr->last_error);
+        }
+    }
+    // ---- host records of every round
+    std::vector<BatchUpd> upd((size_t)R * G);
+    std::vector<VEdge> entries;
+    std::vector<BatchEOp> eops;
+    std::vector<int64_t> eop_off(R + 1, 0);
+    std::vector<int64_t> voff((size_t)R * 4 * (G + 1), 0);
+    std::vector<std::vector<EOp>> gops(G);
+    for (int32_t r = 0; r < R; ++r) {
+        for (int32_t g = 0; g < G; ++g) {
+            BatchUpd& u = upd[(size_t)r * G + g];
+            u = BatchUpd{};
+            if (r >= ok[g]) continue;
+            bc_graph* gr = b->graphs[g];
+            const std::vector<VEdge>& ent = ents[g][r];
+            std::vector<EOp> ops;
+            std::vector<HArc> arcs;
+            bool rebuild = false;
+            mirror_update(gr, vtx[g][r], ent, ops, arcs, &rebuild);
+            if (rebuild) return bfail(b, BC_ERR_CUDA, "internal: E* slack sized too small");
+            u.v = vtx[g][r];
+            u.k = (int32_t)ent.size();
+            u.present = 1;
+            u.first = (int64_t)entries.size();
+            for (const VEdge& e : ent) {
+                if (!gr->directed || e.dir == 0) u.kin++;
+                if (!gr->directed || e.dir == 1) u.kout++;
+                entries.push_back(e);
+            }
+            for (const EOp& op : ops) eops.push_back(BatchEOp{g, 0, op});
+            gr->launches += 20;
+        }
+        eop_off[r + 1] = (int64_t)eops.size();
+        for (int kind = 0; kind < 4; ++kind) {
+            int64_t* o = &voff[((size_t)r * 4 + kind) * (G + 1)];
+            for (int32_t g = 0; g < G; ++g) {
+                const BatchUpd& u = upd[(size_t)r * G + g];
+                const bool on = u.present && (kind == 0 ? u.kin > 0 : u.kout > 0);
+                o[g + 1] = o[g] + (on ? b->graphs[g]->n : 0);
+            }
+        }
+    }
+    // ---- device buffers and launch shape
+    int64_t cap_max = 0;
+    for (bc_graph* g : b->graphs) cap_max = std::max(cap_max, g->d.e_cap);
+    if (cap_max != b->cap_max) {
+        b->cap_max = cap_max;
+        batch_config(b->L, b->dbytes, b->n_max, cap_max);
+        drop_exec(b);
+    }
+    int rc;
+    const int64_t ws_need = (int64_t)b->L.acc_grid * b->L.ws_stride;
+    if (ws_need > b->ws_cap) {
+        bfree(b, b->d_ws);
+        if ((rc = balloc(b, &b->d_ws, ws_need))) return rc;
+        b->ws_cap = ws_need;
+        drop_exec(b);
+    }
+    if (R > b->R_cap) {
+        bfree(b, b->d_upd);
+        bfree(b, b->d_eop_off);
+        bfree(b, b->d_voff);
+        const int64_t rc2 = std::max<int64_t>(R, 8);
+        if ((rc = balloc(b, &b->d_upd, rc2 * G)) || (rc = balloc(b, &b->d_eop_off, rc2 + 1)) ||
+            (rc = balloc(b, &b->d_voff, rc2 * 4 * (G + 1))))
+            return rc;
+        b->R_cap = rc2;
+        drop_exec(b);
+    }
+    if ((int64_t)entries.size() > b->E_cap) {
+        bfree(b, b->d_entries);
+        const int64_t c = std::max<int64_t>((int64_t)entries.size() * 2, 1024);
+        if ((rc = balloc(b, &b->d_entries, c))) return rc;
+        b->E_cap = c;
+        drop_exec(b);
+    }
+    if ((int64_t)eops.size() > b->O_cap) {
+        bfree(b, b->d_eops);
+        const int64_t c = std::max<int64_t>((int64_t)eops.size() * 2, 1024);
+        if ((rc = balloc(b, &b->d_eops, c))) return rc;
+        b->O_cap = c;
+        drop_exec(b);
+    }
+    std::vector<Dev> devs(G);
+    for (int32_t g = 0; g < G; ++g) devs[g] = b->graphs[g]->d;
+    CKB(b, cudaMemcpyAsync(b->d_devs, devs.data(), sizeof(Dev) * G, cudaMemcpyHostToDevice, b->st));
+    if (R > 0) {
+        CKB(b, cudaMemcpyAsync(b->d_upd, upd.data(), sizeof(BatchUpd) * upd.size(), cudaMemcpyHostToDevice, b->st));
+        CKB(b, cudaMemcpyAsync(b->d_eop_off, eop_off.data(), sizeof(int64_t) * eop_off.size(), cudaMemcpyHostToDevice,
+                               b->st));
+        CKB(b, cudaMemcpyAsync(b->d_voff, voff.data(), sizeof(int64_t) * voff.size(), cudaMemcpyHostToDevice, b->st));
+    }
+    if (!entries.empty())
+        CKB(b, cudaMemcpyAsync(b->d_entries, entries.data(), sizeof(VEdge) * entries.size(), cudaMemcpyHostToDevice,
+                               b->st));
+    if (!eops.empty())
+        CKB(b, cudaMemcpyAsync(b->d_eops, eops.data(), sizeof(BatchEOp) * eops.size(), cudaMemcpyHostToDevice, b->st));
+    BatchArgs& a = b->args;
+    a.G = G;
+    a.mask_in_smem = b->L.mask_in_smem;
+    a.devs = b->d_devs;
+    a.upd = b->d_upd;
+    a.entries = b->d_entries;
+    a.eops = b->d_eops;
+    a.eop_off = b->d_eop_off;
+    a.voff = b->d_voff;
+    a.coff = b->d_coff;
+    a.plan_scan = b->d_plans;
+    a.plan_bc = b->d_plans + (G + 1);
+    a.plan_acc = b->d_plans + 2 * (G + 1);
+    a.ws = b->d_ws;
+    a.ws_stride = b->L.ws_stride;
+    b->L.max_eops = std::max<int64_t>(b->L.max_eops, 256);
+    if (R > 0 && (!b->exec || b->exec_rounds != R)) {
+        drop_exec(b);
+        cudaGraph_t graph = nullptr;
+        CKB(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        batch_launch_rounds(a, b->L, R, b->dbytes, b->st);
+        CKB(b, cudaStreamEndCapture(b->st, &graph));
+        cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(b, BC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        b->exec_rounds = R;
+    }
+    CKB(b, cudaEventRecord(b->e0, b->st));
+    if (R > 0) CKB(b, cudaGraphLaunch(b->exec, b->st));
+    CKB(b, cudaEventRecord(b->e1, b->st));
+    CKB(b, cudaStreamSynchronize(b->st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->e0, b->e1);
+    b->last_ms = ms;
+    for (int32_t g = 0; g < G; ++g) {
+        bc_graph* gr = b->graphs[g];
+        int rg = sync_check(gr);
+        if (rg != BC_OK && status == BC_OK) {
+            status = rg;
+            b->last_error = gr->last_error;
+        }
+        if (n_done) n_done[g] = ok[g];
+    }
+    return status;
+}
+
+int bc_batch_last_ms(bc_batch* b, double* ms) {
+    if (!b || !ms) return BC_ERR_ARG;
+    *ms = b->last_ms;
+    return BC_OK;
+}
+
+const char* bc_batch_last_error(const bc_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+void bc_batch_destroy(bc_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    drop_exec(b);
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->e0) cudaEventDestroy(b->e0);
+    if (b->e1) cudaEventDestroy(b->e1);
+    if (b->own_stream) cudaStreamDestroy(b->st);
+    delete b;
 }
 
 }  // extern "C"

@@ -1,0 +1,60 @@
+// bc_batch.cuh -- device-side records of a batch of graphs (k_batch.cu) and the launch
+// entry points the host side of the batch calls.
+#pragma once
+
+#include "bc_internal.cuh"
+
+namespace bcg {
+
+// The r-th update of graph g (rounds x graphs, row-major by round).
+struct BatchUpd {
+    int32_t v;        // the updated vertex (an edge update (u, v) is one in-edge of v)
+    int32_t k;        // its edges, entries[first .. first + k)
+    int32_t kin;      // edges into v (IN phase), edges out of v (OUT phase)
+    int32_t kout;
+    int32_t present;  // 0: graph g has no r-th update
+    int32_t pad;
+    int64_t first;
+};
+
+struct BatchEOp {
+    int32_t g;
+    int32_t pad;
+    EOp op;
+};
+
+struct BatchArgs {
+    int32_t G;
+    int32_t mask_in_smem;
+    const Dev* devs;          // [G]
+    const BatchUpd* upd;      // [rounds * G]
+    const VEdge* entries;
+    const BatchEOp* eops;
+    const int64_t* eop_off;   // [rounds + 1]
+    const int64_t* voff;      // [rounds * 4 * (G + 1)]: per-vertex pass offsets
+    const int64_t* coff;      // [G + 1]: column offsets (prefix of n_g)
+    int64_t* plan_scan;       // [G + 1]
+    int64_t* plan_bc;         // [G + 1]
+    int64_t* plan_acc;        // [G + 1]
+    int32_t* ws;              // accumulation work space, acc_grid * ws_stride ints
+    int64_t ws_stride;
+};
+
+// Launch shape of a batch; the tunable part is what the autotuner varies.
+struct BatchLaunch {
+    int32_t nsm;
+    int32_t vpass_ctas;   // CTAs per SM of the per-vertex passes      (tunable)
+    int32_t scan_ctas;    // CTAs per SM of the rank-1 pass             (tunable)
+    int32_t bc_ctas;      // CTAs per SM of the BC row sums             (tunable)
+    int32_t acc_per_sm;   // cap on accumulation CTAs per SM, 0 = max   (tunable)
+    int32_t acc_grid;
+    int32_t acc_smem;
+    int32_t mask_in_smem;
+    int64_t ws_stride;
+    int64_t max_eops;
+};
+
+void batch_config(BatchLaunch& L, int dbytes, int n_max, int64_t cap_max);
+void batch_launch_rounds(const BatchArgs& b, const BatchLaunch& L, int rounds, int dbytes, cudaStream_t st);
+
+}  // namespace bcg

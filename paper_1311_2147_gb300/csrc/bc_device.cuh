@@ -1,0 +1,815 @@
+// bc_device.cuh -- device functions shared by the single-graph kernels and the batched
+// (many graphs per launch) kernels, so that both run the same arithmetic and give
+// bit-identical results.  What each function computes is described at its definition;
+// the translation units that launch them describe the method (k_update.cu: the
+// all-pairs passes; k_accum.cu: the dependency accumulation and BC).
+#pragma once
+
+#include "bc_internal.cuh"
+
+namespace bcg {
+
+// Algorithm 4 (Compute-Dist-to-v) for source s = this thread, over the in-edges
+// (x_j, v) of the update, followed by the affected-row test of the IN phase: row s can
+// change only if d'(s,v) < d(s,v) or new shortest paths reach v (sigma-hat > 0).
+template <typename DT>
+__device__ __forceinline__ void dev_alg4_in(int s, int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
+                          int v, const VEdge* __restrict__ e, int k, int directed,
+                          DT* fD, uint64_t* fS, uint64_t* fM, uint8_t* mark, uint8_t* changed,
+                          int32_t* err) {
+    const int64_t INF = Inf<DT>::v;
+    const size_t rs = (size_t)s * n;
+    const int64_t old = D[rs + v];
+    int64_t cur = old;
+    uint64_t sig = S[rs + v];
+    uint64_t hat = 0;
+    bool sat = false;
+    for (int j = 0; j < k; ++j) {
+        const VEdge ed = e[j];
+        if (directed && ed.dir != 0) continue;
+        const int64_t dx = D[rs + ed.x];
+        if (dx == INF) continue;
+        const int64_t dj = dsum<DT>(dx, ed.w);
+        if (dj == SAT) {
+            sat = true;
+            continue;
+        }
+        const uint64_t sx = S[rs + ed.x];
+        if (cur == dj) {
+            sig = add_chk(sig, sx, err);
+            hat += sx;
+        } else if (cur > dj) {
+            cur = dj;
+            sig = sx;
+        }
+    }
+    // v reachable from s only through a sum that does not fit: d'(s,v) overflows.
+    if (sat && cur == INF) set_err(err, ERRF_DIST);
+    const bool dec = cur < old;
+    const bool aff = dec || hat != 0;
+    fD[s] = (DT)cur;
+    fS[s] = sig;
+    fM[s] = dec ? sig : hat;
+    mark[s] = aff ? 1 : 0;
+    if (aff) changed[s] = 1;
+}
+
+// OUT phase, row test: row s (s != v) can change only through a new shortest path
+// s ~> v -> x_j, i.e. d'(s,v) + w'(v,x_j) <= d'(s,x_j) for some out-edge of the update.
+template <typename DT>
+__device__ __forceinline__ void dev_rows_out(int s, int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
+                           int v, const VEdge* __restrict__ e, int k, int directed,
+                           DT* fD, uint64_t* fS, uint64_t* fM, uint8_t* mark, uint8_t* changed,
+                           int32_t* err) {
+    const int64_t INF = Inf<DT>::v;
+    const size_t rs = (size_t)s * n;
+    const int64_t dsv = D[rs + v];
+    const uint64_t ssv = S[rs + v];
+    bool aff = false;
+    if (s != v && dsv != INF) {
+        for (int j = 0; j < k; ++j) {
+            const VEdge ed = e[j];
+            if (directed && ed.dir != 1) continue;
+            const int64_t dy = D[rs + ed.x];
+            const int64_t c = dsum<DT>(dsv, ed.w);
+            // A sum that does not fit can only matter where d'(s,x_j) is INF; the row is
+            // then kept so that the scan decides (and reports a distance overflow).
+            if (c == SAT) {
+                if (dy == INF) aff = true;
+                continue;
+            }
+            if (c <= dy) aff = true;
+        }
+    }
+    fD[s] = (DT)dsv;
+    fS[s] = ssv;
+    fM[s] = ssv;
+    mark[s] = aff ? 1 : 0;
+    if (aff) changed[s] = 1;
+}
+
+// Algorithm 4 on the reversed graph G'_R, for "source" t of G'_R = target t of G: the
+// out-edges (v, x_j) of the update are in-edges of v in G'_R, and d_R(t, x_j) is
+// d'(x_j, t), read from row x_j.  Produces row v of the result.
+template <typename DT>
+__device__ __forceinline__ void dev_alg4_out(int t, int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
+                           int v, const VEdge* __restrict__ e, int k, int directed,
+                           DT* cD, uint64_t* cS, uint64_t* cM, uint8_t* changed, int32_t* err) {
+    const int64_t INF = Inf<DT>::v;
+    const size_t rv = (size_t)v * n;
+    const int64_t old = D[rv + t];
+    int64_t cur = old;
+    uint64_t sig = S[rv + t];
+    uint64_t hat = 0;
+    bool sat = false;
+    for (int j = 0; j < k; ++j) {
+        const VEdge ed = e[j];
+        if (directed && ed.dir != 1) continue;
+        const size_t ry = (size_t)ed.x * n;
+        const int64_t dy = D[ry + t];
+        if (dy == INF) continue;
+        const int64_t dj = dsum<DT>(ed.w, dy);
+        if (dj == SAT) {
+            sat = true;
+            continue;
+        }
+        const uint64_t sy = S[ry + t];
+        if (cur == dj) {
+            sig = add_chk(sig, sy, err);
+            hat += sy;
+        } else if (cur > dj) {
+            cur = dj;
+            sig = sy;
+        }
+    }
+    if (sat && cur == INF) set_err(err, ERRF_DIST);
+    const bool dec = cur < old;
+    cD[t] = (DT)cur;
+    cS[t] = sig;
+    cM[t] = dec ? sig : hat;
+    if (dec || hat != 0) changed[v] = 1;
+}
+
+// Stable compaction of {s : mark[s]} (or of all s when full) into rows[], one CTA.
+// Optionally clears mark[] and accumulates the per-update counters.
+constexpr int kCompactThreads = 1024;
+// Every thread of the block calls it; blockDim.x is a multiple of 32 (at most 1024).
+__device__ __forceinline__ void dev_compact(int n, uint8_t* mark, int clear, int32_t* rows, int32_t* count,
+                                            int full, int64_t* stats, const int32_t* err) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t s_total;
+    const int nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool bad = *err != 0;
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
+    for (int tile = 0; tile < n; tile += blockDim.x) {
+        const int s = tile + tid;
+        int f = 0;
+        if (s < n) {
+            f = (!bad && (full || mark[s] != 0)) ? 1 : 0;
+            if (clear) mark[s] = 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int wpre = __popc(bal & lt);
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        if (wid == 0) {
+            const int x = lane < nwarps ? wsum[lane] : 0;
+            int incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane < nwarps) wsum[lane] = incl - x;
+            if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+        if (f) rows[base + wsum[wid] + wpre] = s;
+        base += s_total;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *count = base;
+        if (stats) {
+            stats[0] += base;
+            if (base == 0) stats[1] += 1;
+            if (base > stats[2]) stats[2] = base;
+            stats[3] += 1;
+        }
+    }
+}
+
+// Vector access of VEC consecutive distances (16 bytes).
+template <typename DT> struct Vec;
+template <> struct Vec<int32_t> {
+    static constexpr int N = 4;
+    using T = int4;
+    __device__ static void unpack(const T& x, int64_t* o) { o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; }
+    __device__ static void set(T& x, int i, int64_t val) {
+        if (i == 0) x.x = (int32_t)val; else if (i == 1) x.y = (int32_t)val;
+        else if (i == 2) x.z = (int32_t)val; else x.w = (int32_t)val;
+    }
+};
+template <> struct Vec<int64_t> {
+    static constexpr int N = 2;
+    using T = longlong2;
+    __device__ static void unpack(const T& x, int64_t* o) { o[0] = x.x; o[1] = x.y; }
+    __device__ static void set(T& x, int i, int64_t val) { if (i == 0) x.x = val; else x.y = val; }
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanUnroll = 4;
+
+template <typename DT>
+struct ScanArgs {
+    int n;
+    DT* D;
+    uint64_t* S;
+    const int32_t* rows;
+    const int32_t* count;
+    const DT* fD;          // per row s: distance to v (after the IN phase)
+    const uint64_t* fS;    // per row s: path count to v
+    const uint64_t* fM;    // per row s: multiplier of a tie
+    const DT* cD;          // per column t: distance from v
+    const uint64_t* cS;    // per column t: path count from v
+    const uint64_t* cM;    // per column t: multiplier of a tie
+    int skip_row;
+    int32_t* err;
+    int64_t* stats;        // [4] pairs with a lower distance [5] pairs with new tied paths [6] rows
+};
+
+// The rank-1 rule of Lemma 2 / Lemma 4 for one pair, given the candidate distance
+// cand = rd + cd through v:  cand > d: unchanged;  cand == d: sigma += rowM * colM
+// (new shortest paths through v);  cand < d: d = cand, sigma = rowS * colS.
+template <typename DT>
+__device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx, uint64_t rs,
+                                          uint64_t rm, uint64_t cs, uint64_t cm,
+                                          uint64_t* S, int32_t* err, int64_t* newd, int* ties) {
+    if (cand == SAT) {
+        if (old == Inf<DT>::v) set_err(err, ERRF_DIST);
+        return false;
+    }
+    if (cand > old) return false;
+    if (cand < old) {
+        S[idx] = mul_chk(rs, cs, err);
+        *newd = cand;
+        return true;
+    }
+    const uint64_t p = mul_chk(rm, cm, err);
+    if (p != 0ull) {
+        S[idx] = add_chk(S[idx], p, err);
+        ++*ties;
+    }
+    return false;
+}
+
+// One work item of the rank-1 pass: row s (scalars rd, rs, rm), chunk c of CW columns.
+template <typename DT, bool VECTOR>
+__device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int64_t rd, uint64_t rs, uint64_t rm,
+                                              int c, int& n_changed, int& n_ties) {
+    using V = Vec<DT>;
+    constexpr int VN = V::N;
+    constexpr int CW = kScanThreads * VN * kScanUnroll;
+    const int n = a.n;
+    const int64_t INF = Inf<DT>::v;
+    const size_t rowoff = (size_t)s * n;
+    DT* __restrict__ Drow = a.D + rowoff;
+    const int t0 = c * CW;
+    const int tid = threadIdx.x % kScanThreads;
+    if constexpr (VECTOR) {
+        typename V::T dv[kScanUnroll], cv[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+            const int t = t0 + (u * kScanThreads + tid) * VN;
+            if (t < n) {
+                dv[u] = __ldcs(reinterpret_cast<const typename V::T*>(Drow + t));
+                cv[u] = __ldg(reinterpret_cast<const typename V::T*>(a.cD + t));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+            const int t = t0 + (u * kScanThreads + tid) * VN;
+            if (t >= n) break;
+            bool any = false;
+            if constexpr (sizeof(DT) == 4) {
+                // both terms are below 2^31, so their sum fits 32 bits: a pair can change
+                // only if the column term is finite and the sum does not exceed d (or d
+                // is INF, where a sum that does not fit must be reported)
+                const uint32_t r32 = (uint32_t)rd;
+                const int32_t* dp = reinterpret_cast<const int32_t*>(&dv[u]);
+                const int32_t* cp = reinterpret_cast<const int32_t*>(&cv[u]);
+#pragma unroll
+                for (int q = 0; q < VN; ++q) {
+                    const uint32_t sum = r32 + (uint32_t)cp[q];
+                    any |= (cp[q] != INT32_MAX) & ((sum <= (uint32_t)dp[q]) | (dp[q] == INT32_MAX));
+                }
+            } else {
+                int64_t dd0[VN], cd0[VN];
+                V::unpack(dv[u], dd0);
+                V::unpack(cv[u], cd0);
+#pragma unroll
+                for (int q = 0; q < VN; ++q) {
+                    if (cd0[q] == INF) continue;
+                    const int64_t cand = dsum<DT>(rd, cd0[q]);
+                    any |= (cand <= dd0[q]) || (cand == SAT);
+                }
+            }
+            if (!any) continue;
+            int64_t dd[VN], cd[VN];
+            V::unpack(dv[u], dd);
+            V::unpack(cv[u], cd);
+            bool wr = false;
+#pragma unroll
+            for (int q = 0; q < VN; ++q) {
+                if (cd[q] == INF) continue;
+                const int64_t cand = dsum<DT>(rd, cd[q]);
+                int64_t nd;
+                if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q],
+                                  a.S, a.err, &nd, &n_ties)) {
+                    V::set(dv[u], q, nd);
+                    wr = true;
+                    ++n_changed;
+                }
+            }
+            if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv[u];
+        }
+    } else {
+        for (int t = t0 + tid; t < t0 + CW && t < n; t += kScanThreads) {
+            const int64_t cd = a.cD[t];
+            if (cd == INF) continue;
+            const int64_t old = Drow[t];
+            const int64_t cand = dsum<DT>(rd, cd);
+            int64_t nd;
+            if (pair_rule<DT>(cand, old, rowoff + t, rs, rm, a.cS[t], a.cM[t], a.S, a.err, &nd, &n_ties)) {
+                Drow[t] = (DT)nd;
+                ++n_changed;
+            }
+        }
+    }
+}
+
+// Fold the per-thread counters of the scan into the handle's statistics (whole warps).
+__device__ __forceinline__ void scan_stats(int64_t* stats, int n_changed, int n_ties) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_changed += __shfl_xor_sync(0xffffffffu, n_changed, o);
+        n_ties += __shfl_xor_sync(0xffffffffu, n_ties, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (n_changed | n_ties)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats + 4), (unsigned long long)n_changed);
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats + 5), (unsigned long long)n_ties);
+    }
+}
+
+template <typename DT>
+__device__ __forceinline__ void dev_write_row(int t, int n, DT* D, uint64_t* S, int v, const DT* cD, const uint64_t* cS,
+                            const int32_t* err) {
+    D[(size_t)v * n + t] = cD[t];
+    S[(size_t)v * n + t] = cS[t];
+}
+
+template <typename DT>
+struct AccArgs {
+    int n;
+    const DT* D;
+    uint64_t* S;
+    ff* Dl;
+    const int32_t* e_off;
+    const int32_t* e_len;
+    const int32_t* e_src;
+    const Arc<DT>* e_arc;
+    int64_t e_cap;
+    const int32_t* e_big;
+    int e_nbig;
+    const int32_t* rows;
+    const int32_t* count;
+    int32_t* ws;
+    int64_t ws_stride;
+    int32_t* err;
+    int mask_in_smem;
+};
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+// Distance of vertex i of the current source, with the row's own INF marker.
+struct Dist16 {
+    const uint16_t* p;
+    static constexpr uint64_t INFV = 0xFFFFull;
+    __device__ __forceinline__ uint64_t operator()(int i) const { return p[i]; }
+};
+template <typename DT>
+struct DistG {
+    const DT* p;
+    static constexpr uint64_t INFV = (uint64_t)Inf<DT>::v;
+    __device__ __forceinline__ uint64_t operator()(int i) const { return (uint64_t)(int64_t)__ldg(p + i); }
+};
+
+// Arc (x -> b, w) is in DAG'(s): d(x) finite (checked by the caller), d(b) finite and
+// d(x) + w == d(b).
+template <typename DA>
+__device__ __forceinline__ bool on_dag(const DA& dist, uint64_t dx, int b, uint64_t w) {
+    const uint64_t db = dist(b);
+    return db != DA::INFV && dx + w == db;
+}
+
+// 16-bit in-degree counters, two to a 32-bit word (in-degrees stay below 65536).
+__device__ __forceinline__ void cnt_inc(uint32_t* cnt, int b) {
+    atomicAdd(cnt + (b >> 1), 1u << ((b & 1) << 4));
+}
+__device__ __forceinline__ bool cnt_last(uint32_t* cnt, int b) {
+    const uint32_t sh = (b & 1) << 4;
+    return ((atomicSub(cnt + (b >> 1), 1u << sh) >> sh) & 0xFFFFu) == 1u;
+}
+
+// Append the lanes' ready vertices to the order with one shared atomic per warp.
+__device__ __forceinline__ void warp_append(bool ready, int b, uint16_t* order, int* tail) {
+    const unsigned bal = __ballot_sync(FULL, ready);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(tail, __popc(bal));
+    base = __shfl_sync(FULL, base, __ffs(bal) - 1);
+    if (ready) order[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)b;
+}
+
+__device__ __forceinline__ ff warp_sum(ff x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_xor(x, o));
+    return x;
+}
+
+// Finish vertex x: delta(x) = sigma_sx * acc, rho(x) = (1 + delta(x)) / sigma_sx
+// = acc + 1 / sigma_sx.
+__device__ __forceinline__ void finish_vertex(int x, ff acc, uint64_t sigma, ff* out, ff* rho) {
+    const ff sx = ff_from_u64(sigma);
+    out[x] = ff_mul(sx, acc);
+    rho[x] = ff_add(acc, ff_rcp(sx));
+}
+
+// Passes 2 and 3 walk only the arcs of DAG'(s): pass 1 evaluates the predicate once per
+// slot of the E* superset and records it in a bit mask (one warp ballot per 32 slots).
+// Within a level, the DAG arcs of the level's vertices are spread evenly over the
+// threads: a block scan of the vertices' DAG out-degrees gives each arc a rank, a
+// thread finds the owner of its rank by binary search and the arc by selecting the
+// right set bit of the owner's slot range.  In pass 3 the arcs' contributions go to a
+// shared buffer and each owner adds its own in rank order (deterministic).  Vertices
+// with more than kBigDag DAG out-arcs are taken by whole warps instead (lanes over
+// their slots, fixed butterfly), so no owner loops long.
+constexpr int kBigDag = 32;
+constexpr int kBigCap = 2048;
+
+__device__ __forceinline__ int count_bits(const uint32_t* m, int beg, int end) {
+    if (beg >= end) return 0;
+    const int w0 = beg >> 5, w1 = (end - 1) >> 5;
+    int c = 0;
+    for (int w = w0; w <= w1; ++w) {
+        uint32_t b = m[w];
+        if (w == w0) b &= 0xffffffffu << (beg & 31);
+        if (w == w1) b &= 0xffffffffu >> (31 - ((end - 1) & 31));
+        c += __popc(b);
+    }
+    return c;
+}
+
+// Slot of the r-th (0-based) set bit of m within [beg, end); the bit exists.
+__device__ __forceinline__ int select_bit(const uint32_t* m, int beg, int end, int r) {
+    const int w1 = (end - 1) >> 5;
+    int w = beg >> 5;
+    uint32_t b = m[w] & (0xffffffffu << (beg & 31));
+    for (;;) {
+        if (w == w1) b &= 0xffffffffu >> (31 - ((end - 1) & 31));
+        const int c = __popc(b);
+        if (r < c) break;
+        r -= c;
+        b = m[++w];
+    }
+    for (; r > 0; --r) b &= b - 1u;
+    return (w << 5) + __ffs(b) - 1;
+}
+
+// Exclusive block-wide prefix sum of v (all threads call it); *total gets the sum.
+// s_ws needs kAccThreads / 32 + 1 ints and must not be reused before a barrier.
+__device__ __forceinline__ int block_excl_scan(int v, int* s_ws, int* total) {
+    constexpr int NW = kAccThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < NW ? s_ws[lane] : 0;
+        int ix = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, ix, o);
+            if (lane >= o) ix += y;
+        }
+        if (lane < NW) s_ws[lane] = ix - x;
+        if (lane == NW - 1) s_ws[NW] = ix;
+    }
+    __syncthreads();
+    *total = s_ws[NW];
+    return s_ws[warp] + incl - v;
+}
+
+// Last index i in [0, kAccThreads) with off[i] <= j (off non-decreasing, off[0] = 0).
+__device__ __forceinline__ int owner_of(const int* off, int j) {
+    int lo = 0, hi = kAccThreads;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Append x to the big list when there is room (warp-aggregated); returns whether it was.
+__device__ __forceinline__ bool big_push(bool want, int x, uint16_t* big, int* nbig) {
+    const unsigned bal = __ballot_sync(FULL, want);
+    if (!bal) return false;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(nbig, __popc(bal));
+    base = __shfl_sync(FULL, base, __ffs(bal) - 1);
+    const int pos = base + __popc(bal & ((1u << lane) - 1u));
+    if (want && pos < kBigCap) {
+        big[pos] = (uint16_t)x;
+        return true;
+    }
+    return false;
+}
+
+template <typename DT, bool STATIC>
+__device__ __forceinline__ void push_sigma(uint64_t* Ss, int b, uint64_t sx, int32_t* err) {
+    if (STATIC) {
+        const unsigned long long old =
+            atomicAdd(reinterpret_cast<unsigned long long*>(Ss + b), (unsigned long long)sx);
+        if (old + sx < old) set_err(err, ERRF_OVERFLOW);
+    }
+}
+
+// Per-round shared scratch of the level passes.
+struct LevelSmem {
+    int off[kAccThreads];
+    int beg[kAccThreads];
+    int end[kAccThreads];
+    uint64_t sx[kAccThreads];
+    ff buf[kAccThreads];
+    int ws[kAccThreads / 32 + 1];
+};
+
+template <typename DT, bool STATIC, typename DA>
+__device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA dist, int s, uint64_t* Ss,
+                                                  ff* out, uint32_t* cnt, uint16_t* order, uint32_t* mask,
+                                                  uint16_t* big, LevelSmem& ls, ff* rho, int32_t* lvl,
+                                                  int* s_tail, int* s_nbig) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int T = kAccThreads, NW = kAccThreads / 32, U = 4;
+    // ---- pass 1: DAG'(s) membership of every slot, and in-degrees (loads of U chunks
+    // are issued before any of them is used)
+    const int nchunk = (int)((a.e_cap + 31) >> 5);
+    for (int c0 = warp; c0 < nchunk; c0 += U * NW) {
+        Arc<DT> r[U];
+        int src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = ((int64_t)(c0 + u * NW) << 5) + lane;
+            r[u].dst = -1;
+            src[u] = 0;
+            if (e < a.e_cap) {
+                r[u] = a.e_arc[e];
+                src[u] = a.e_src[e];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + u * NW;
+            if (c >= nchunk) break;
+            const int b = (int)r[u].dst;
+            bool on = false;
+            if (b >= 0) {
+                const uint64_t dx = dist(src[u]);
+                on = dx != DA::INFV && on_dag(dist, dx, b, (uint64_t)r[u].w);
+            }
+            if (on) cnt_inc(cnt, b);
+            const unsigned word = __ballot_sync(FULL, on);
+            if (lane == 0) mask[c] = word;
+        }
+    }
+    __syncthreads();   // the distance row (aliased by order) is dead from here on
+    if (tid == 0) {
+        order[0] = (uint16_t)s;
+        lvl[0] = 0;
+        lvl[1] = 1;
+        *s_tail = 1;
+        *s_nbig = 0;
+    }
+    __syncthreads();
+    // ---- pass 2: Kahn levels (statically also the forward path counts)
+    int L = 0;
+    for (;;) {
+        const int lo = lvl[L], hi = lvl[L + 1];
+        for (int qb = lo; qb < hi; qb += T) {
+            const int q = qb + tid;
+            int x = 0, beg = 0, end = 0, k = 0;
+            if (q < hi) {
+                x = order[q];
+                beg = a.e_off[x];
+                end = beg + a.e_len[x];
+                k = count_bits(mask, beg, end);
+            }
+            if (big_push(k > kBigDag, x, big, s_nbig)) k = 0;
+            int total;
+            const int off = block_excl_scan(k, ls.ws, &total);
+            ls.off[tid] = off;
+            ls.beg[tid] = beg;
+            ls.end[tid] = end;
+            if (STATIC) ls.sx[tid] = k ? Ss[x] : 0ull;
+            __syncthreads();
+            for (int jb = 0; jb < total; jb += T) {
+                const int j = jb + tid;
+                bool ready = false;
+                int b = 0;
+                if (j < total) {
+                    const int o = owner_of(ls.off, j);
+                    const int e = select_bit(mask, ls.beg[o], ls.end[o], j - ls.off[o]);
+                    b = (int)a.e_arc[e].dst;
+                    push_sigma<DT, STATIC>(Ss, b, STATIC ? ls.sx[o] : 0ull, a.err);
+                    ready = cnt_last(cnt, b);
+                }
+                warp_append(ready, b, order, s_tail);
+            }
+            __syncthreads();
+        }
+        const int nb = min(*s_nbig, kBigCap);
+        for (int i = warp; i < nb; i += NW) {
+            const int x = big[i];
+            const int beg = a.e_off[x], end = beg + a.e_len[x];
+            const uint64_t sx = STATIC ? Ss[x] : 0ull;
+            for (int eb = beg; eb < end; eb += 32) {
+                const int e = eb + lane;
+                bool ready = false;
+                int b = 0;
+                if (e < end && ((mask[e >> 5] >> (e & 31)) & 1u)) {
+                    b = (int)a.e_arc[e].dst;
+                    push_sigma<DT, STATIC>(Ss, b, sx, a.err);
+                    ready = cnt_last(cnt, b);
+                }
+                warp_append(ready, b, order, s_tail);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            lvl[L + 2] = *s_tail;
+            *s_nbig = 0;
+        }
+        __syncthreads();
+        if (lvl[L + 2] == hi) break;
+        ++L;
+    }
+    // ---- pass 3: Eq. 4 in reverse level order (level 0 is s: delta_s.(s) is not kept)
+    for (int Lq = L; Lq >= 1; --Lq) {
+        const int lo = lvl[Lq], hi = lvl[Lq + 1];
+        for (int qb = lo; qb < hi; qb += T) {
+            const int q = qb + tid;
+            int x = 0, beg = 0, end = 0, k = 0;
+            if (q < hi) {
+                x = order[q];
+                beg = a.e_off[x];
+                end = beg + a.e_len[x];
+                k = count_bits(mask, beg, end);
+            }
+            const bool is_big = big_push(k > kBigDag, x, big, s_nbig);
+            if (is_big) k = 0;
+            const bool mine = q < hi && !is_big;
+            const uint64_t sig = mine ? Ss[x] : 1ull;
+            int total;
+            const int off = block_excl_scan(k, ls.ws, &total);
+            ls.off[tid] = off;
+            ls.beg[tid] = beg;
+            ls.end[tid] = end;
+            __syncthreads();
+            ff acc{0.0f, 0.0f};
+            for (int jb = 0; jb < total; jb += T) {
+                const int j = jb + tid;
+                if (j < total) {
+                    const int o = owner_of(ls.off, j);
+                    const int e = select_bit(mask, ls.beg[o], ls.end[o], j - ls.off[o]);
+                    ls.buf[tid] = rho[a.e_arc[e].dst];
+                }
+                __syncthreads();
+                const int p0 = max(off, jb), p1 = min(off + k, jb + T);
+                for (int p = p0; p < p1; ++p) acc = ff_add(acc, ls.buf[p - jb]);
+                __syncthreads();
+            }
+            if (mine) finish_vertex(x, acc, sig, out, rho);
+        }
+        __syncthreads();
+        const int nb = min(*s_nbig, kBigCap);
+        for (int i = warp; i < nb; i += NW) {
+            const int x = big[i];
+            const int beg = a.e_off[x], end = beg + a.e_len[x];
+            ff acc{0.0f, 0.0f};
+            for (int e = beg + lane; e < end; e += 32)
+                if ((mask[e >> 5] >> (e & 31)) & 1u) acc = ff_add(acc, rho[a.e_arc[e].dst]);
+            acc = warp_sum(acc);
+            if (lane == 0) finish_vertex(x, acc, Ss[x], out, rho);
+        }
+        __syncthreads();
+        if (tid == 0) *s_nbig = 0;
+        __syncthreads();
+    }
+}
+
+// Shared-memory layout of the accumulation kernel for n vertices (n rounded to np):
+// [d16 | order] (2np bytes; the distance row is dead once the slot mask is built, so
+// the level order reuses it) | cnt (np/2 words) | big list | slot mask (here when it
+// fits, else in the work space).
+struct AccSmem {
+    uint16_t* d16;
+    uint16_t* order;
+    uint32_t* cnt;
+    uint16_t* big;
+    uint32_t* mask;
+    ff* rho;
+    int32_t* lvl;
+};
+
+template <typename DT>
+__device__ __forceinline__ AccSmem acc_smem(const AccArgs<DT>& a, unsigned char* smem, int32_t* wsb) {
+    const int n = a.n;
+    const int np = (n + 31) & ~31;
+    AccSmem m;
+    m.d16 = reinterpret_cast<uint16_t*>(smem);
+    m.order = m.d16;
+    m.cnt = reinterpret_cast<uint32_t*>(smem + 2 * (size_t)np);
+    m.big = reinterpret_cast<uint16_t*>(smem + 4 * (size_t)np);
+    m.rho = reinterpret_cast<ff*>(wsb);
+    m.lvl = wsb + 2 * (size_t)n;
+    m.mask = a.mask_in_smem ? reinterpret_cast<uint32_t*>(smem + 4 * (size_t)np + 2 * kBigCap)
+                            : reinterpret_cast<uint32_t*>(wsb + ((3 * (int64_t)n + 2 + 3) & ~(int64_t)3));
+    return m;
+}
+
+// Re-accumulate source s (whole block; every thread calls it): stage its distance row,
+// rebuild DAG'(s), order it, pull Eq. 4, write its delta row (and, statically, its
+// sigma row).
+template <typename DT, bool STATIC>
+__device__ __forceinline__ void dev_accum_source(const AccArgs<DT>& a, int s, const AccSmem& m, LevelSmem& ls,
+                                                 int* s_tail, int* s_nbig) {
+    const int n = a.n;
+    const int np = (n + 31) & ~31;
+    const int tid = threadIdx.x;
+    const int64_t INF = Inf<DT>::v;
+    const DT* Ds = a.D + (size_t)s * n;
+    uint64_t* Ss = a.S + (size_t)s * n;
+    ff* out = a.Dl + (size_t)s * n;
+    int wide = 0;
+    for (int t = tid; t < n; t += kAccThreads) {
+        const int64_t v = Ds[t];
+        uint16_t c;
+        if (v == INF) c = 0xFFFF;
+        else if (v < 0xFFFF) c = (uint16_t)v;
+        else { c = 0xFFFE; wide = 1; }
+        m.d16[t] = c;
+        out[t] = ff{0.0f, 0.0f};
+        if (STATIC) Ss[t] = (t == s) ? 1ull : 0ull;
+    }
+    for (int t = tid; t < np / 2; t += kAccThreads) m.cnt[t] = 0u;
+    wide = __syncthreads_or(wide);
+    if (!wide)
+        accumulate_source<DT, STATIC>(a, Dist16{m.d16}, s, Ss, out, m.cnt, m.order, m.mask, m.big, ls, m.rho, m.lvl,
+                                      s_tail, s_nbig);
+    else
+        accumulate_source<DT, STATIC>(a, DistG<DT>{Ds}, s, Ss, out, m.cnt, m.order, m.mask, m.big, ls, m.rho, m.lvl,
+                                      s_tail, s_nbig);
+    __syncthreads();
+}
+
+// partial[rb][t] = sum over rows r of row block rb of Dl[s_r][t] (t != s_r), rows in
+// increasing order, in float-float (all terms are non-negative); rows = nullptr means
+// all n rows.
+__device__ __forceinline__ void dev_bc_partial(int t, int rb, int n, const int32_t* rows, int total,
+                                               const ff* Dl, ff* partial) {
+    const int r0 = rb * kRowsPerBlock;
+    if (r0 >= total || t >= n) return;
+    const int r1 = min(total, r0 + kRowsPerBlock);
+    ff acc{0.0f, 0.0f};
+    for (int r = r0; r < r1; ++r) {
+        const int s = rows ? rows[r] : r;
+        if (s != t) acc = ff_add(acc, Dl[(size_t)s * n + t]);
+    }
+    partial[(size_t)rb * n + t] = acc;
+}
+
+// bc (hi, lo) += sign * (sum of the row-block partials in block order): the partials are
+// summed in float-float, the total is taken to fp64 and added with TwoSum; overwrite
+// starts from zero (the static computation).
+__device__ __forceinline__ void dev_bc_finish(int t, int n, int total, const ff* partial, double sign,
+                                              int overwrite, double* hi, double* lo) {
+    const int nrb = (total + kRowsPerBlock - 1) / kRowsPerBlock;
+    if (nrb == 0 && !overwrite) return;
+    ff acc{0.0f, 0.0f};
+    for (int rb = 0; rb < nrb; ++rb) acc = ff_add(acc, partial[(size_t)rb * n + t]);
+    const double sum = sign * ff_to_double(acc);
+    if (overwrite) {
+        hi[t] = sum;
+        lo[t] = 0.0;
+        return;
+    }
+    // TwoSum (Knuth): h + x = s + e exactly
+    const double h = hi[t];
+    const double s = h + sum;
+    const double bp = s - h;
+    const double e = (h - (s - bp)) + (sum - bp);
+    hi[t] = s;
+    lo[t] += e;
+}
+
+}  // namespace bcg

@@ -19,7 +19,7 @@
 //
 // Lemma 1 (and its vertex analogue) makes the in-place scan race free: during the IN
 // phase row v and column x_j are never written, during the OUT phase column v is not.
-#include "bc_internal.cuh"
+#include "bc_device.cuh"
 
 namespace bcg {
 
@@ -35,9 +35,6 @@ __global__ void k_estar_write(int32_t* e_src, void* e_arc, int32_t* e_len, int d
     atomicMax(e_len + o.a, o.len_a);   // lengths only grow between rebuilds
 }
 
-// Algorithm 4 (Compute-Dist-to-v) for source s = this thread, over the in-edges
-// (x_j, v) of the update, followed by the affected-row test of the IN phase: row s can
-// change only if d'(s,v) < d(s,v) or new shortest paths reach v (sigma-hat > 0).
 template <typename DT>
 __global__ void k_alg4_in(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
                           int v, const VEdge* __restrict__ e, int k, int directed,
@@ -45,46 +42,9 @@ __global__ void k_alg4_in(int n, const DT* __restrict__ D, const uint64_t* __res
                           int32_t* err) {
     if (*err) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int64_t INF = Inf<DT>::v;
-    const size_t rs = (size_t)s * n;
-    const int64_t old = D[rs + v];
-    int64_t cur = old;
-    uint64_t sig = S[rs + v];
-    uint64_t hat = 0;
-    bool sat = false;
-    for (int j = 0; j < k; ++j) {
-        const VEdge ed = e[j];
-        if (directed && ed.dir != 0) continue;
-        const int64_t dx = D[rs + ed.x];
-        if (dx == INF) continue;
-        const int64_t dj = dsum<DT>(dx, ed.w);
-        if (dj == SAT) {
-            sat = true;
-            continue;
-        }
-        const uint64_t sx = S[rs + ed.x];
-        if (cur == dj) {
-            sig = add_chk(sig, sx, err);
-            hat += sx;
-        } else if (cur > dj) {
-            cur = dj;
-            sig = sx;
-        }
-    }
-    // v reachable from s only through a sum that does not fit: d'(s,v) overflows.
-    if (sat && cur == INF) set_err(err, ERRF_DIST);
-    const bool dec = cur < old;
-    const bool aff = dec || hat != 0;
-    fD[s] = (DT)cur;
-    fS[s] = sig;
-    fM[s] = dec ? sig : hat;
-    mark[s] = aff ? 1 : 0;
-    if (aff) changed[s] = 1;
+    if (s < n) dev_alg4_in<DT>(s, n, D, S, v, e, k, directed, fD, fS, fM, mark, changed, err);
 }
 
-// OUT phase, row test: row s (s != v) can change only through a new shortest path
-// s ~> v -> x_j, i.e. d'(s,v) + w'(v,x_j) <= d'(s,x_j) for some out-edge of the update.
 template <typename DT>
 __global__ void k_rows_out(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
                            int v, const VEdge* __restrict__ e, int k, int directed,
@@ -92,191 +52,22 @@ __global__ void k_rows_out(int n, const DT* __restrict__ D, const uint64_t* __re
                            int32_t* err) {
     if (*err) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int64_t INF = Inf<DT>::v;
-    const size_t rs = (size_t)s * n;
-    const int64_t dsv = D[rs + v];
-    const uint64_t ssv = S[rs + v];
-    bool aff = false;
-    if (s != v && dsv != INF) {
-        for (int j = 0; j < k; ++j) {
-            const VEdge ed = e[j];
-            if (directed && ed.dir != 1) continue;
-            const int64_t dy = D[rs + ed.x];
-            const int64_t c = dsum<DT>(dsv, ed.w);
-            // A sum that does not fit can only matter where d'(s,x_j) is INF; the row is
-            // then kept so that the scan decides (and reports a distance overflow).
-            if (c == SAT) {
-                if (dy == INF) aff = true;
-                continue;
-            }
-            if (c <= dy) aff = true;
-        }
-    }
-    fD[s] = (DT)dsv;
-    fS[s] = ssv;
-    fM[s] = ssv;
-    mark[s] = aff ? 1 : 0;
-    if (aff) changed[s] = 1;
+    if (s < n) dev_rows_out<DT>(s, n, D, S, v, e, k, directed, fD, fS, fM, mark, changed, err);
 }
 
-// Algorithm 4 on the reversed graph G'_R, for "source" t of G'_R = target t of G: the
-// out-edges (v, x_j) of the update are in-edges of v in G'_R, and d_R(t, x_j) is
-// d'(x_j, t), read from row x_j.  Produces row v of the result.
 template <typename DT>
 __global__ void k_alg4_out(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
                            int v, const VEdge* __restrict__ e, int k, int directed,
                            DT* cD, uint64_t* cS, uint64_t* cM, uint8_t* changed, int32_t* err) {
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int64_t INF = Inf<DT>::v;
-    const size_t rv = (size_t)v * n;
-    const int64_t old = D[rv + t];
-    int64_t cur = old;
-    uint64_t sig = S[rv + t];
-    uint64_t hat = 0;
-    bool sat = false;
-    for (int j = 0; j < k; ++j) {
-        const VEdge ed = e[j];
-        if (directed && ed.dir != 1) continue;
-        const size_t ry = (size_t)ed.x * n;
-        const int64_t dy = D[ry + t];
-        if (dy == INF) continue;
-        const int64_t dj = dsum<DT>(ed.w, dy);
-        if (dj == SAT) {
-            sat = true;
-            continue;
-        }
-        const uint64_t sy = S[ry + t];
-        if (cur == dj) {
-            sig = add_chk(sig, sy, err);
-            hat += sy;
-        } else if (cur > dj) {
-            cur = dj;
-            sig = sy;
-        }
-    }
-    if (sat && cur == INF) set_err(err, ERRF_DIST);
-    const bool dec = cur < old;
-    cD[t] = (DT)cur;
-    cS[t] = sig;
-    cM[t] = dec ? sig : hat;
-    if (dec || hat != 0) changed[v] = 1;
+    if (t < n) dev_alg4_out<DT>(t, n, D, S, v, e, k, directed, cD, cS, cM, changed, err);
 }
 
-// Stable compaction of {s : mark[s]} (or of all s when full) into rows[], one CTA.
-// Optionally clears mark[] and accumulates the per-update counters.
-constexpr int kCompactThreads = 1024;
 __global__ void __launch_bounds__(kCompactThreads)
 k_compact(int n, uint8_t* mark, int clear, int32_t* rows, int32_t* count, int full,
           int64_t* stats, const int32_t* err) {
-    __shared__ int32_t wsum[32];
-    __shared__ int32_t s_total;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool bad = *err != 0;
-    const unsigned lt = (1u << lane) - 1u;
-    int base = 0;
-    for (int tile = 0; tile < n; tile += kCompactThreads) {
-        const int s = tile + tid;
-        int f = 0;
-        if (s < n) {
-            f = (!bad && (full || mark[s] != 0)) ? 1 : 0;
-            if (clear) mark[s] = 0;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const int wpre = __popc(bal & lt);
-        if (lane == 0) wsum[wid] = __popc(bal);
-        __syncthreads();
-        if (wid == 0) {
-            const int x = wsum[lane];
-            int incl = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            wsum[lane] = incl - x;
-            if (lane == 31) s_total = incl;
-        }
-        __syncthreads();
-        if (f) rows[base + wsum[wid] + wpre] = s;
-        base += s_total;
-        __syncthreads();
-    }
-    if (tid == 0) {
-        *count = base;
-        if (stats) {
-            stats[0] += base;
-            if (base == 0) stats[1] += 1;
-            if (base > stats[2]) stats[2] = base;
-            stats[3] += 1;
-        }
-    }
-}
-
-// Vector access of VEC consecutive distances (16 bytes).
-template <typename DT> struct Vec;
-template <> struct Vec<int32_t> {
-    static constexpr int N = 4;
-    using T = int4;
-    __device__ static void unpack(const T& x, int64_t* o) { o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; }
-    __device__ static void set(T& x, int i, int64_t val) {
-        if (i == 0) x.x = (int32_t)val; else if (i == 1) x.y = (int32_t)val;
-        else if (i == 2) x.z = (int32_t)val; else x.w = (int32_t)val;
-    }
-};
-template <> struct Vec<int64_t> {
-    static constexpr int N = 2;
-    using T = longlong2;
-    __device__ static void unpack(const T& x, int64_t* o) { o[0] = x.x; o[1] = x.y; }
-    __device__ static void set(T& x, int i, int64_t val) { if (i == 0) x.x = val; else x.y = val; }
-};
-
-constexpr int kScanThreads = 256;
-constexpr int kScanUnroll = 4;
-
-template <typename DT>
-struct ScanArgs {
-    int n;
-    DT* D;
-    uint64_t* S;
-    const int32_t* rows;
-    const int32_t* count;
-    const DT* fD;          // per row s: distance to v (after the IN phase)
-    const uint64_t* fS;    // per row s: path count to v
-    const uint64_t* fM;    // per row s: multiplier of a tie
-    const DT* cD;          // per column t: distance from v
-    const uint64_t* cS;    // per column t: path count from v
-    const uint64_t* cM;    // per column t: multiplier of a tie
-    int skip_row;
-    int32_t* err;
-    int64_t* stats;        // [4] pairs with a lower distance [5] pairs with new tied paths [6] rows
-};
-
-// The rank-1 rule of Lemma 2 / Lemma 4 for one pair, given the candidate distance
-// cand = rd + cd through v:  cand > d: unchanged;  cand == d: sigma += rowM * colM
-// (new shortest paths through v);  cand < d: d = cand, sigma = rowS * colS.
-template <typename DT>
-__device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx, uint64_t rs,
-                                          uint64_t rm, uint64_t cs, uint64_t cm,
-                                          uint64_t* S, int32_t* err, int64_t* newd, int* ties) {
-    if (cand == SAT) {
-        if (old == Inf<DT>::v) set_err(err, ERRF_DIST);
-        return false;
-    }
-    if (cand > old) return false;
-    if (cand < old) {
-        S[idx] = mul_chk(rs, cs, err);
-        *newd = cand;
-        return true;
-    }
-    const uint64_t p = mul_chk(rm, cm, err);
-    if (p != 0ull) {
-        S[idx] = add_chk(S[idx], p, err);
-        ++*ties;
-    }
-    return false;
+    dev_compact(n, mark, clear, rows, count, full, stats, err);
 }
 
 // K2: in-place rank-1 min-plus / path-count pass over rows[0..count) x all columns.
@@ -290,11 +81,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
     int bad = 0;
     if ((threadIdx.x & 31) == 0) bad = *reinterpret_cast<volatile int32_t*>(a.err);
     if (__shfl_sync(0xffffffffu, bad, 0)) return;
-    using V = Vec<DT>;
-    constexpr int VN = V::N;
-    constexpr int CW = kScanThreads * VN * kScanUnroll;
-    const int n = a.n;
-    const int nchunks = (n + CW - 1) / CW;
+    constexpr int CW = kScanThreads * Vec<DT>::N * kScanUnroll;
+    const int nchunks = (a.n + CW - 1) / CW;
     const int64_t total = (int64_t)(*a.count) * nchunks;
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t it0 = (int64_t)blockIdx.x * per;
@@ -317,89 +105,9 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
             rm = a.fM[s];
         }
         if (rd == INF) continue;
-        const size_t rowoff = (size_t)s * n;
-        DT* __restrict__ Drow = a.D + rowoff;
-        const int t0 = c * CW;
-        if constexpr (VECTOR) {
-            typename V::T dv[kScanUnroll], cv[kScanUnroll];
-#pragma unroll
-            for (int u = 0; u < kScanUnroll; ++u) {
-                const int t = t0 + (u * kScanThreads + threadIdx.x) * VN;
-                if (t < n) {
-                    dv[u] = __ldcs(reinterpret_cast<const typename V::T*>(Drow + t));
-                    cv[u] = __ldg(reinterpret_cast<const typename V::T*>(a.cD + t));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kScanUnroll; ++u) {
-                const int t = t0 + (u * kScanThreads + threadIdx.x) * VN;
-                if (t >= n) break;
-                bool any = false;
-                if constexpr (sizeof(DT) == 4) {
-                    // both terms are below 2^31, so their sum fits 32 bits: a pair can change
-                    // only if the column term is finite and the sum does not exceed d (or d
-                    // is INF, where a sum that does not fit must be reported)
-                    const uint32_t r32 = (uint32_t)rd;
-                    const int32_t* dp = reinterpret_cast<const int32_t*>(&dv[u]);
-                    const int32_t* cp = reinterpret_cast<const int32_t*>(&cv[u]);
-#pragma unroll
-                    for (int q = 0; q < VN; ++q) {
-                        const uint32_t sum = r32 + (uint32_t)cp[q];
-                        any |= (cp[q] != INT32_MAX) & ((sum <= (uint32_t)dp[q]) | (dp[q] == INT32_MAX));
-                    }
-                } else {
-                    int64_t dd0[VN], cd0[VN];
-                    V::unpack(dv[u], dd0);
-                    V::unpack(cv[u], cd0);
-#pragma unroll
-                    for (int q = 0; q < VN; ++q) {
-                        if (cd0[q] == INF) continue;
-                        const int64_t cand = dsum<DT>(rd, cd0[q]);
-                        any |= (cand <= dd0[q]) || (cand == SAT);
-                    }
-                }
-                if (!any) continue;
-                int64_t dd[VN], cd[VN];
-                V::unpack(dv[u], dd);
-                V::unpack(cv[u], cd);
-                bool wr = false;
-#pragma unroll
-                for (int q = 0; q < VN; ++q) {
-                    if (cd[q] == INF) continue;
-                    const int64_t cand = dsum<DT>(rd, cd[q]);
-                    int64_t nd;
-                    if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q],
-                                      a.S, a.err, &nd, &n_ties)) {
-                        V::set(dv[u], q, nd);
-                        wr = true;
-                        ++n_changed;
-                    }
-                }
-                if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv[u];
-            }
-        } else {
-            for (int t = t0 + threadIdx.x; t < t0 + CW && t < n; t += kScanThreads) {
-                const int64_t cd = a.cD[t];
-                if (cd == INF) continue;
-                const int64_t old = Drow[t];
-                const int64_t cand = dsum<DT>(rd, cd);
-                int64_t nd;
-                if (pair_rule<DT>(cand, old, rowoff + t, rs, rm, a.cS[t], a.cM[t], a.S, a.err, &nd, &n_ties)) {
-                    Drow[t] = (DT)nd;
-                    ++n_changed;
-                }
-            }
-        }
+        dev_scan_item<DT, VECTOR>(a, s, rd, rs, rm, c, n_changed, n_ties);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n_changed += __shfl_xor_sync(0xffffffffu, n_changed, o);
-        n_ties += __shfl_xor_sync(0xffffffffu, n_ties, o);
-    }
-    if ((threadIdx.x & 31) == 0 && (n_changed | n_ties)) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 4), (unsigned long long)n_changed);
-        atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 5), (unsigned long long)n_ties);
-    }
+    scan_stats(a.stats, n_changed, n_ties);
 }
 
 template <typename DT>
@@ -407,9 +115,7 @@ __global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, cons
                             const int32_t* err) {
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    D[(size_t)v * n + t] = cD[t];
-    S[(size_t)v * n + t] = cS[t];
+    if (t < n) dev_write_row<DT>(t, n, D, S, v, cD, cS, err);
 }
 
 // keep[e] = 1 when slot e holds an arc (a,b) with w(a,b) == d(a,b), i.e. an arc of E*
