@@ -235,10 +235,11 @@ class EdgeMap:
     directed: bool
     w: dict = field(default_factory=dict)
     adj: list = field(default_factory=list)
+    keys: list = field(default_factory=list)   # keys in insertion order (for sampling)
 
     @classmethod
     def of(cls, g: Graph) -> "EdgeMap":
-        em = cls(g.n, g.directed, {}, [set() for _ in range(g.n)])
+        em = cls(g.n, g.directed, {}, [set() for _ in range(g.n)], [])
         for a, b, x in zip(g.src.tolist(), g.dst.tolist(), g.w.tolist()):
             em.set(a, b, x)
         return em
@@ -257,6 +258,7 @@ class EdgeMap:
             self.adj[a].add(b)
             if not self.directed:
                 self.adj[b].add(a)
+            self.keys.append(k)
         self.w[k] = x
 
     def to_graph(self) -> Graph:
@@ -295,10 +297,13 @@ def _draw_edge_update(em: EdgeMap, rng: Rng, new_edge: bool, wlo: int, whi: int)
             if u != v and em.get(u, v) is None:
                 return ("edge", u, v, int(rng.uniform_int(wlo, whi, 1)[0]))
         raise RuntimeError("no free pair for a new edge")
-    keys = [k for k, x in em.w.items() if x >= 2]
-    if not keys:
+    # a uniformly drawn existing edge of weight >= 2 (rejection sampling)
+    for _ in range(100000):
+        a, b = em.keys[rng.one(len(em.keys))]
+        if em.w[(a, b)] >= 2:
+            break
+    else:
         raise RuntimeError("no edge with weight >= 2 to decrease")
-    a, b = keys[rng.one(len(keys))]
     if not em.directed and rng.one(2):
         a, b = b, a
     old = em.w[em.key(a, b)]
@@ -415,7 +420,7 @@ def log_uniform_n(rng: Rng, lo: int, hi: int, k: int) -> list:
 
 
 def workload_batch(seed: int = BASE_SEED + 3, count: int = 512, nlo: int = 64, nhi: int = 2048,
-                   n_updates: int = 8):
+                   n_updates: int = 8, rounds: int = 1):
     """count graphs, n log-uniform in [nlo, nhi]; even index directed ER (out-degree 8),
     odd index undirected BA(8); w ~ U[1,1000]; n_updates edge updates each."""
     rng = Rng(seed)
@@ -427,7 +432,8 @@ def workload_batch(seed: int = BASE_SEED + 3, count: int = 512, nlo: int = 64, n
             g = erdos_renyi_degree(n, 8, 1, 1000, gs)
         else:
             g = barabasi_albert(max(n, 9), 8, 1, 1000, gs)
-        half = n_updates // 2
-        ups = update_stream(g, half, n_updates - half, 0, sub_seed(seed, 2 * i + 11), 1, 1000)
+        total = n_updates * rounds
+        half = total // 2
+        ups = update_stream(g, half, total - half, 0, sub_seed(seed, 2 * i + 11), 1, 1000)
         out.append((g, ups))
     return out
