@@ -301,6 +301,68 @@ const char* bc_batch_last_error(const bc_batch* b);
 /* bc_batch_destroy -- free the batch (not the graphs). */
 void bc_batch_destroy(bc_batch* b);
 
+/*
+ * bc_get_edges -- the current edges of the graph (undirected: each edge once, a < b),
+ * sorted, into host arrays of *m entries.  Call with src = dst = w = NULL to get the
+ * count in *m.  Enough to rebuild the state later with bc_init_static.
+ */
+int bc_get_edges(bc_graph* g, int64_t* m, int32_t* src, int32_t* dst, int64_t* w);
+
+/*
+ * Serving.  A server keeps many graphs resident on the device and applies update
+ * requests to them as they arrive.  Requests for one graph are applied in arrival
+ * order; whenever a graph has nothing on the device, all its queued requests are
+ * launched together on its own stream (continuous batching), so requests that arrive
+ * while it is busy join its next launch and different graphs' launches overlap.  A
+ * graph's device state (about n^2 * (distance bytes + 16) bytes) is built only when
+ * the budget and the device's free memory leave room; when a graph with queued
+ * requests needs room, idle graphs are evicted least-recently-used first and rebuilt
+ * from their current edges when needed again.  Results are the same as applying each
+ * graph's requests to it alone (same kernels, same order).  Not thread-safe: drive a
+ * server from one host thread.
+ */
+typedef struct bc_server bc_server;
+
+typedef struct bc_result {
+    int64_t request_id;
+    int32_t graph_id;
+    int32_t status;       /* bc_status of the request */
+    int64_t latency_ns;   /* submission to the poll that saw it finished */
+} bc_result;
+
+/* bc_server_create -- budget: device bytes the server may use for graph states;
+ * max_batch: most requests of one graph launched together (<= 0: 64). */
+int bc_server_create(bc_server** out, int64_t mem_budget_bytes, int32_t max_batch);
+
+/* bc_server_add_graph -- register a graph (arguments as bc_init_static; host arrays are
+ * copied).  It is built on the device now if there is room, otherwise when it first has
+ * a request and room can be made.  *graph_id receives its index. */
+int bc_server_add_graph(bc_server* s, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                        const int64_t* w, uint32_t flags, int32_t* graph_id);
+
+/* bc_server_submit -- queue one update for a graph (non-blocking); edges as in
+ * bc_apply_updates for a vertex update (copied).  *request_id (optional) receives its id. */
+int bc_server_submit(bc_server* s, int32_t graph_id, const bc_update* up, const bc_vedge* edges,
+                     int64_t* request_id);
+
+/* bc_server_poll -- non-blocking progress: collect finished launches, admit graphs,
+ * launch queued requests of idle graphs; then copy up to max_results finished requests
+ * to out (host array) and their number to *n_out. */
+int bc_server_poll(bc_server* s, int32_t max_results, bc_result* out, int32_t* n_out);
+
+/* bc_server_pending -- requests still queued, and in flight or not yet collected. */
+int bc_server_pending(bc_server* s, int64_t* queued, int64_t* inflight);
+
+/* bc_server_graph -- the handle of a graph (admitting it if needed, waiting for its
+ * launch in flight); valid until the next server call. */
+int bc_server_graph(bc_server* s, int32_t graph_id, bc_graph** handle);
+
+/* bc_server_stats -- stats[5]: resident graphs, bytes in use, admissions, evictions,
+ * launches. */
+int bc_server_stats(bc_server* s, int64_t* stats);
+
+void bc_server_destroy(bc_server* s);
+
 /* bc_destroy -- free the handle and its device memory (waits for its stream). */
 void bc_destroy(bc_graph* g);
 

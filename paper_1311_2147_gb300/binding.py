@@ -41,7 +41,9 @@ EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "
            "bc_stage_updates", "bc_run_staged", "bc_synchronize", "bc_query", "bc_get_scores",
            "bc_get_rows", "bc_get_info", "bc_get_profile", "bc_set_option", "bc_destroy", "bc_last_error",
            "bc_static_scores_noalloc", "bc_batch_create", "bc_batch_apply", "bc_batch_set_tiles",
-           "bc_batch_last_ms", "bc_batch_last_error", "bc_batch_destroy"]
+           "bc_batch_last_ms", "bc_batch_last_error", "bc_batch_destroy", "bc_get_edges",
+           "bc_server_create", "bc_server_add_graph", "bc_server_submit", "bc_server_poll",
+           "bc_server_pending", "bc_server_graph", "bc_server_stats", "bc_server_destroy"]
 PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping"]
 
 
@@ -53,6 +55,10 @@ class bc_info(ctypes.Structure):
                 ("rows_scanned", ctypes.c_int64), ("pairs_lowered", ctypes.c_int64),
                 ("pairs_tied", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double)]
+
+
+RESULT_DTYPE = np.dtype([("request_id", "<i8"), ("graph_id", "<i4"), ("status", "<i4"),
+                         ("latency_ns", "<i8")], align=True)
 
 
 class BCError(RuntimeError):
@@ -103,6 +109,15 @@ def load(build_if_missing: bool = True):
         "bc_batch_last_ms": ([p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "bc_batch_last_error": ([p], ctypes.c_char_p),
         "bc_batch_destroy": ([p], None),
+        "bc_get_edges": ([p, ctypes.POINTER(i64), p, p, p], ctypes.c_int),
+        "bc_server_create": ([ctypes.POINTER(p), i64, i32], ctypes.c_int),
+        "bc_server_add_graph": ([p, i32, i64, p, p, p, u32, ctypes.POINTER(i32)], ctypes.c_int),
+        "bc_server_submit": ([p, i32, p, p, ctypes.POINTER(i64)], ctypes.c_int),
+        "bc_server_poll": ([p, i32, p, ctypes.POINTER(i32)], ctypes.c_int),
+        "bc_server_pending": ([p, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "bc_server_graph": ([p, i32, ctypes.POINTER(p)], ctypes.c_int),
+        "bc_server_stats": ([p, p], ctypes.c_int),
+        "bc_server_destroy": ([p], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -287,3 +302,93 @@ class BCBatch:
 
     def last_error(self):
         return self.lib.bc_batch_last_error(self.h).decode()
+
+
+class _Borrowed(BCGraph):
+    """A handle owned by a server (not destroyed by Python)."""
+
+    def __init__(self, lib, h, n, directed):
+        self.lib, self.h, self.n, self.directed = lib, h, n, directed
+
+    def close(self):
+        self.h = None
+
+
+class BCServer:
+    """Continuous-batching server over many device-resident graphs."""
+
+    def __init__(self, budget_bytes: int, max_batch: int = 64):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.bc_server_create(ctypes.byref(h), int(budget_bytes), int(max_batch))
+        if rc != BC_OK:
+            raise BCError(rc, "bc_server_create failed")
+        self.h = h
+        self.meta = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_graph(self, g, dist="i32") -> int:
+        src, dst, w = g.arrays()
+        flags = (BC_DIRECTED if g.directed else BC_UNDIRECTED) | (BC_DIST_I32 if dist == "i32" else BC_DIST_I64)
+        gid = ctypes.c_int32(0)
+        rc = self.lib.bc_server_add_graph(self.h, int(g.n), int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(w),
+                                          flags, ctypes.byref(gid))
+        if rc != BC_OK:
+            raise BCError(rc, "bc_server_add_graph failed")
+        self.meta.append((int(g.n), bool(g.directed)))
+        return gid.value
+
+    def submit(self, gid: int, up) -> int:
+        rec, ed = encode_updates([up])
+        rid = ctypes.c_int64(0)
+        rc = self.lib.bc_server_submit(self.h, int(gid), _ptr(rec), _ptr(ed) if ed.size else None, ctypes.byref(rid))
+        if rc != BC_OK:
+            raise BCError(rc, "bc_server_submit failed")
+        return rid.value
+
+    def poll(self, max_results: int = 4096):
+        out = np.zeros(max_results, dtype=RESULT_DTYPE)
+        k = ctypes.c_int32(0)
+        rc = self.lib.bc_server_poll(self.h, int(max_results), _ptr(out), ctypes.byref(k))
+        if rc != BC_OK:
+            raise BCError(rc, "bc_server_poll failed")
+        return out[: k.value]
+
+    def pending(self):
+        q, f = ctypes.c_int64(0), ctypes.c_int64(0)
+        self.lib.bc_server_pending(self.h, ctypes.byref(q), ctypes.byref(f))
+        return q.value, f.value
+
+    def drain(self):
+        res = []
+        while True:
+            r = self.poll()
+            if r.size:
+                res.append(r)
+            q, f = self.pending()
+            if q == 0 and f == 0:
+                break
+        return np.concatenate(res) if res else np.zeros(0, dtype=RESULT_DTYPE)
+
+    def graph(self, gid: int) -> BCGraph:
+        h = ctypes.c_void_p()
+        rc = self.lib.bc_server_graph(self.h, int(gid), ctypes.byref(h))
+        if rc != BC_OK:
+            raise BCError(rc, "bc_server_graph failed")
+        n, directed = self.meta[gid]
+        return _Borrowed(self.lib, h, n, directed)
+
+    def stats(self):
+        st = np.zeros(5, np.int64)
+        self.lib.bc_server_stats(self.h, _ptr(st))
+        return dict(zip(["resident", "bytes", "admissions", "evictions", "launches"], st.tolist()))

@@ -787,6 +787,30 @@ int bc_get_rows(bc_graph* g, int32_t s0, int32_t count, int64_t* d_out, uint64_t
     return BC_OK;
 }
 
+int bc_get_edges(bc_graph* g, int64_t* m, int32_t* src, int32_t* dst, int64_t* w) {
+    if (!g || !m) return BC_ERR_ARG;
+    std::vector<std::pair<uint64_t, int64_t>> e;
+    e.reserve(g->wmap.size());
+    for (const auto& kv : g->wmap) {
+        const int32_t a = (int32_t)(kv.first >> 32), b = (int32_t)(kv.first & 0xffffffffu);
+        if (!g->directed && a > b) continue;
+        e.push_back(kv);
+    }
+    std::sort(e.begin(), e.end());
+    if (!src && !dst && !w) {
+        *m = (int64_t)e.size();
+        return BC_OK;
+    }
+    if (*m < (int64_t)e.size() || !src || !dst || !w) return fail(g, BC_ERR_ARG, "edge arrays too small");
+    for (size_t i = 0; i < e.size(); ++i) {
+        src[i] = (int32_t)(e[i].first >> 32);
+        dst[i] = (int32_t)(e[i].first & 0xffffffffu);
+        w[i] = e[i].second;
+    }
+    *m = (int64_t)e.size();
+    return BC_OK;
+}
+
 int bc_get_info(bc_graph* g, bc_info* out) {
     if (!g || !out) return BC_ERR_ARG;
     CK(g, cudaStreamSynchronize(g->d.st));
