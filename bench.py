@@ -414,6 +414,92 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving workload: 64 resident graphs, n log-uniform in [1024, 8192], alternately
+    directed ER (out-degree 8) and undirected BA(8), w ~ U[1,100]; requests are edge
+    updates or vertex updates on 2..16 edges (half each) for uniformly drawn graphs.
+    Saturated throughput is measured closed-loop (all requests submitted at once), then
+    an open-loop Poisson stream at --serve-load x that rate gives p50/p99 latency."""
+    import torch
+    from paper_1311_2147_gb300 import binding, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    binding.load()
+    seed = synth.BASE_SEED + 4
+    rng = synth.Rng(seed)
+    G = args.serve_graphs
+    ns = synth.log_uniform_n(rng, 1024, 8192, G)
+    graphs = []
+    for i, n in enumerate(ns):
+        g = (synth.erdos_renyi_degree(n, 8, 1, 100, synth.sub_seed(seed, i)) if i % 2 == 0
+             else synth.barabasi_albert(n, 8, 1, 100, synth.sub_seed(seed, i)))
+        graphs.append(g)
+    R = args.serve_requests
+    # requests over uniformly drawn graphs, each stream valid against its own graph
+    pick = rng.below(G, 2 * R + 64).tolist()
+    per_graph = [0] * G
+    for gi in pick:
+        per_graph[gi] += 1
+    streams = []
+    for i, g in enumerate(graphs):
+        k = per_graph[i]
+        ne = k // 2
+        streams.append(synth.update_stream(g, ne // 2, ne - ne // 2, k - ne, synth.sub_seed(seed, 1000 + i),
+                                           1, 100) if k else [])
+    nxt = [0] * G
+    seq = []
+    for gi in pick:
+        seq.append((gi, streams[gi][nxt[gi]]))
+        nxt[gi] += 1
+    state = sum(n * n * 20 for n in ns)
+    srv = binding.BCServer(budget_bytes=int(state * 1.5) + (8 << 30), max_batch=64)
+    gids = [srv.add_graph(g) for g in graphs]
+    # closed loop: saturated throughput on the first half
+    closed = seq[:R]
+    t0 = time.perf_counter()
+    for gi, up in closed:
+        srv.submit(gids[gi], up)
+    res_c = srv.drain()
+    t_closed = time.perf_counter() - t0
+    sat = len(closed) / t_closed
+    # open loop: Poisson arrivals at load x saturated throughput on the second half
+    lam = args.serve_load * sat
+    gaps = -np.log(1.0 - synth.Rng(seed + 1).unit(R)) / lam
+    arrivals = np.cumsum(gaps)
+    opened = seq[R:2 * R]
+    res = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(opened):
+            now = time.perf_counter() - t0
+            while i < len(opened) and arrivals[i] <= now:
+                gi, up = opened[i]
+                srv.submit(gids[gi], up)
+                i += 1
+            r = srv.poll()
+            if r.size:
+                res.append(r)
+        res.append(srv.drain())
+        t_open = time.perf_counter() - t0
+    res = np.concatenate(res)
+    lat = res["latency_ns"] / 1e6
+    st = srv.stats()
+    line = {"metric": "serving: updates/sec and p50/p99 latency over resident graphs",
+            "value": len(opened) / t_open, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": t_open * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32/u64/f64", "data": "synthetic",
+            "config": {"workload": f"{G} graphs n log-uniform [1024,8192], ER/BA, w~U[1,100], "
+                                   f"{R} closed-loop then {R} Poisson requests (half edge, half vertex k 2..16)",
+                       "state_gb": state / 1e9, "saturated_updates_per_s": sat, "load": args.serve_load,
+                       "lambda_per_s": lam},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "closed_loop_failures": int((res_c["status"] != 0).sum()), "open_loop_failures": int((res["status"] != 0).sum()),
+            "server": st, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ncu_case(args):
     """A small case of one kernel class for ncu captures (a few GB on the device at most):
     BA n=8192 (state 1.3 GB, above L2), static init, then either two vertex updates
@@ -447,7 +533,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--per-step", type=int, default=32)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ba16384", choices=["ba16384", "er256", "complete2048", "batch512"])
+    ap.add_argument("--workload", default="ba16384",
+                    choices=["ba16384", "er256", "complete2048", "batch512", "serve"])
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--batch-graphs", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--recompute-runs", type=int, default=3)
@@ -465,6 +555,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

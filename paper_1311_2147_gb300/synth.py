@@ -236,10 +236,11 @@ class EdgeMap:
     w: dict = field(default_factory=dict)
     adj: list = field(default_factory=list)
     keys: list = field(default_factory=list)   # keys in insertion order (for sampling)
+    radj: list = field(default_factory=list)   # in-neighbours (directed graphs)
 
     @classmethod
     def of(cls, g: Graph) -> "EdgeMap":
-        em = cls(g.n, g.directed, {}, [set() for _ in range(g.n)], [])
+        em = cls(g.n, g.directed, {}, [set() for _ in range(g.n)], [], [set() for _ in range(g.n)])
         for a, b, x in zip(g.src.tolist(), g.dst.tolist(), g.w.tolist()):
             em.set(a, b, x)
         return em
@@ -258,6 +259,8 @@ class EdgeMap:
             self.adj[a].add(b)
             if not self.directed:
                 self.adj[b].add(a)
+            else:
+                self.radj[b].add(a)
             self.keys.append(k)
         self.w[k] = x
 
@@ -321,8 +324,7 @@ def _draw_vertex_update(em: EdgeMap, rng: Rng, kmin: int, kmax: int, wlo: int, w
             d = rng.one(2) if em.directed else 1
             decrease = rng.one(2) == 0
             if decrease:
-                nbrs = sorted(x for x in (em.adj[v] if (d == 1 or not em.directed) else
-                                          [a for a in range(n) if v in em.adj[a]])
+                nbrs = sorted(x for x in (em.adj[v] if (d == 1 or not em.directed) else em.radj[v])
                               if (x, d) not in used)
                 cand = [x for x in nbrs
                         if (em.get(v, x) if d == 1 else em.get(x, v)) is not None
