@@ -453,13 +453,12 @@ __device__ __forceinline__ int count_bits(const uint32_t* m, int beg, int end) {
     return c;
 }
 
-// Slot of the r-th (0-based) set bit of m within [beg, end); the bit exists.
-__device__ __forceinline__ int select_bit(const uint32_t* m, int beg, int end, int r) {
-    const int w1 = (end - 1) >> 5;
+// Slot of the r-th (0-based) set bit of m at or after slot beg.  Callers pass r below
+// the number of set bits of the vertex's slot range, so the bit lies inside the range.
+__device__ __forceinline__ int select_bit(const uint32_t* m, int beg, int r) {
     int w = beg >> 5;
     uint32_t b = m[w] & (0xffffffffu << (beg & 31));
     for (;;) {
-        if (w == w1) b &= 0xffffffffu >> (31 - ((end - 1) & 31));
         const int c = __popc(b);
         if (r < c) break;
         r -= c;
@@ -535,11 +534,14 @@ __device__ __forceinline__ void push_sigma(uint64_t* Ss, int b, uint64_t sx, int
 }
 
 // Per-round shared scratch of the level passes.
+// A round of a level pass gives every thread up to kPerThread vertices of the level.
+constexpr int kPerThread = 2;
+
 struct LevelSmem {
-    int off[kAccThreads];
-    int beg[kAccThreads];
-    int end[kAccThreads];
-    uint64_t sx[kAccThreads];
+    int off[kAccThreads];                  // first arc rank of the thread's vertices
+    int beg[kPerThread][kAccThreads];      // slot range start of each vertex
+    int k0[kAccThreads];                   // DAG out-arcs of the thread's first vertex
+    uint64_t sx[kPerThread][kAccThreads];  // path counts (static pass 2)
     ff buf[kAccThreads];
     int ws[kAccThreads / 32 + 1];
 };
@@ -550,7 +552,7 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                                                   uint16_t* big, LevelSmem& ls, ff* rho, int32_t* lvl,
                                                   int* s_tail, int* s_nbig) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int T = kAccThreads, NW = kAccThreads / 32, U = 4;
+    constexpr int T = kAccThreads, NW = kAccThreads / 32, U = 8;
     // ---- pass 1: DAG'(s) membership of every slot, and in-degrees (loads of U chunks
     // are issued before any of them is used)
     const int nchunk = (int)((a.e_cap + 31) >> 5);
@@ -595,22 +597,28 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
     int L = 0;
     for (;;) {
         const int lo = lvl[L], hi = lvl[L + 1];
-        for (int qb = lo; qb < hi; qb += T) {
-            const int q = qb + tid;
-            int x = 0, beg = 0, end = 0, k = 0;
-            if (q < hi) {
-                x = order[q];
-                beg = a.e_off[x];
-                end = beg + a.e_len[x];
-                k = count_bits(mask, beg, end);
+        for (int qb = lo; qb < hi; qb += kPerThread * T) {
+            int kk[kPerThread];
+            int kt = 0;
+#pragma unroll
+            for (int v = 0; v < kPerThread; ++v) {
+                const int q = qb + v * T + tid;
+                int x = 0, beg = 0, k = 0;
+                if (q < hi) {
+                    x = order[q];
+                    beg = a.e_off[x];
+                    k = count_bits(mask, beg, beg + a.e_len[x]);
+                }
+                if (big_push(k > kBigDag, x, big, s_nbig)) k = 0;
+                kk[v] = k;
+                kt += k;
+                ls.beg[v][tid] = beg;
+                if (STATIC) ls.sx[v][tid] = k ? Ss[x] : 0ull;
             }
-            if (big_push(k > kBigDag, x, big, s_nbig)) k = 0;
             int total;
-            const int off = block_excl_scan(k, ls.ws, &total);
+            const int off = block_excl_scan(kt, ls.ws, &total);
             ls.off[tid] = off;
-            ls.beg[tid] = beg;
-            ls.end[tid] = end;
-            if (STATIC) ls.sx[tid] = k ? Ss[x] : 0ull;
+            ls.k0[tid] = kk[0];
             __syncthreads();
             for (int jb = 0; jb < total; jb += T) {
                 const int j = jb + tid;
@@ -618,9 +626,12 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                 int b = 0;
                 if (j < total) {
                     const int o = owner_of(ls.off, j);
-                    const int e = select_bit(mask, ls.beg[o], ls.end[o], j - ls.off[o]);
+                    int r = j - ls.off[o];
+                    const int v = r < ls.k0[o] ? 0 : 1;
+                    if (v) r -= ls.k0[o];
+                    const int e = select_bit(mask, ls.beg[v][o], r);
                     b = (int)a.e_arc[e].dst;
-                    push_sigma<DT, STATIC>(Ss, b, STATIC ? ls.sx[o] : 0ull, a.err);
+                    push_sigma<DT, STATIC>(Ss, b, STATIC ? ls.sx[v][o] : 0ull, a.err);
                     ready = cnt_last(cnt, b);
                 }
                 warp_append(ready, b, order, s_tail);
@@ -656,39 +667,60 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
     // ---- pass 3: Eq. 4 in reverse level order (level 0 is s: delta_s.(s) is not kept)
     for (int Lq = L; Lq >= 1; --Lq) {
         const int lo = lvl[Lq], hi = lvl[Lq + 1];
-        for (int qb = lo; qb < hi; qb += T) {
-            const int q = qb + tid;
-            int x = 0, beg = 0, end = 0, k = 0;
-            if (q < hi) {
-                x = order[q];
-                beg = a.e_off[x];
-                end = beg + a.e_len[x];
-                k = count_bits(mask, beg, end);
+        for (int qb = lo; qb < hi; qb += kPerThread * T) {
+            int xs[kPerThread], kk[kPerThread];
+            uint64_t sig[kPerThread];
+            bool mine[kPerThread];
+            int kt = 0;
+#pragma unroll
+            for (int v = 0; v < kPerThread; ++v) {
+                const int q = qb + v * T + tid;
+                int x = 0, beg = 0, k = 0;
+                if (q < hi) {
+                    x = order[q];
+                    beg = a.e_off[x];
+                    k = count_bits(mask, beg, beg + a.e_len[x]);
+                }
+                const bool is_big = big_push(k > kBigDag, x, big, s_nbig);
+                if (is_big) k = 0;
+                mine[v] = q < hi && !is_big;
+                sig[v] = mine[v] ? Ss[x] : 1ull;
+                xs[v] = x;
+                kk[v] = k;
+                kt += k;
+                ls.beg[v][tid] = beg;
             }
-            const bool is_big = big_push(k > kBigDag, x, big, s_nbig);
-            if (is_big) k = 0;
-            const bool mine = q < hi && !is_big;
-            const uint64_t sig = mine ? Ss[x] : 1ull;
             int total;
-            const int off = block_excl_scan(k, ls.ws, &total);
+            const int off = block_excl_scan(kt, ls.ws, &total);
             ls.off[tid] = off;
-            ls.beg[tid] = beg;
-            ls.end[tid] = end;
+            ls.k0[tid] = kk[0];
             __syncthreads();
-            ff acc{0.0f, 0.0f};
+            ff acc[kPerThread];
+#pragma unroll
+            for (int v = 0; v < kPerThread; ++v) acc[v] = ff{0.0f, 0.0f};
             for (int jb = 0; jb < total; jb += T) {
                 const int j = jb + tid;
                 if (j < total) {
                     const int o = owner_of(ls.off, j);
-                    const int e = select_bit(mask, ls.beg[o], ls.end[o], j - ls.off[o]);
+                    int r = j - ls.off[o];
+                    const int v = r < ls.k0[o] ? 0 : 1;
+                    if (v) r -= ls.k0[o];
+                    const int e = select_bit(mask, ls.beg[v][o], r);
                     ls.buf[tid] = rho[a.e_arc[e].dst];
                 }
                 __syncthreads();
-                const int p0 = max(off, jb), p1 = min(off + k, jb + T);
-                for (int p = p0; p < p1; ++p) acc = ff_add(acc, ls.buf[p - jb]);
+                int p = off;
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    const int p0 = max(p, jb), p1 = min(p + kk[v], jb + T);
+                    for (int pp = p0; pp < p1; ++pp) acc[v] = ff_add(acc[v], ls.buf[pp - jb]);
+                    p += kk[v];
+                }
                 __syncthreads();
             }
-            if (mine) finish_vertex(x, acc, sig, out, rho);
+#pragma unroll
+            for (int v = 0; v < kPerThread; ++v)
+                if (mine[v]) finish_vertex(xs[v], acc[v], sig[v], out, rho);
         }
         __syncthreads();
         const int nb = min(*s_nbig, kBigCap);
