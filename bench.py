@@ -344,16 +344,19 @@ def run_ours(args):
 
     if rank == 0:
         rows_per_upd = (info1["rows_reaccumulated"] - info0["rows_reaccumulated"]) / len(timed)
+        per_update = {k: (info1[k] - info0[k]) / len(timed)
+                      for k in ("rows_reaccumulated", "rows_full", "rows_scanned", "pairs_lowered", "pairs_tied",
+                                "estar_moves", "estar_rebuilds")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int32/u64/f64" if dtype == "i32" else "int64/u64/f64", "data": "synthetic",
                 "config": {"workload": desc, "updates_per_step": U,
-                           "l2": f"state {n * n * (sd + 16) / 1e9:.2f} GB per graph > 129 MB L2; no flush",
+                           "l2": f"state {n * n * (sd + 16 + (0 if g.directed else sd + 8)) / 1e9:.2f} GB per graph > 129 MB L2; no flush",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clk.summary(), "gpu_full_recompute": gpu_full,
                 "latency_ms": {"p50": e2e["p50_ms"], "p99": e2e["p99_ms"]} if e2e else None,
-                "classes": classes, "rows_per_update": rows_per_upd}
+                "classes": classes, "rows_per_update": rows_per_upd, "per_update": per_update}
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()

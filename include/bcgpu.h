@@ -113,6 +113,10 @@ typedef struct bc_info {
     int64_t kernel_launches;     /* kernels enqueued by this handle since init */
     int64_t state_bytes;         /* device bytes owned by the handle */
     double last_init_ms;         /* device time of the static computation in bc_init_static */
+    int64_t rows_full;           /* of rows_reaccumulated: rows rebuilt by Algorithm 1 rather than
+                                    corrected pair by pair ("pair_updates") */
+    int64_t estar_rebuilds;      /* times the E* superset was laid out again (host round trip) */
+    int64_t estar_moves;         /* vertex segments of E* moved to the free region instead */
 } bc_info;
 
 /*
@@ -217,10 +221,11 @@ int bc_get_info(bc_graph* g, bc_info* out);
  * each launch on the handle's stream).  Classes: 0 the rank-1 pass (Lemma 2 / 4),
  * 1 dependency accumulation (Eq. 4 / Algorithm 1), 2 BC row sums, 3 per-vertex passes
  * (Algorithm 4 in both directions, row tests, row write), 4 bookkeeping (compaction,
- * E* writes).  ms and launches are host arrays of BC_PROFILE_CLASSES entries (either
+ * E* writes, flags), 5 saving rows before their first write, 6 pair corrections of the
+ * dependency rows ("pair_updates").  ms and launches are host arrays of BC_PROFILE_CLASSES entries (either
  * may be NULL).  reset != 0 clears the sums after reading.  Synchronous.
  */
-enum { BC_PROFILE_CLASSES = 5 };
+enum { BC_PROFILE_CLASSES = 7 };
 int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
 
 /*
@@ -228,6 +233,15 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
  *   "full_scan" 0|1: run the rank-1 pass of Lemma 2 / 4 over every row instead of
  *                     only the rows that can change (Section 5 scans all n^2 pairs).
  *   "profile"   0|1: record CUDA events around every launch (see bc_get_profile).
+ *   "pair_updates" 0|1 (undirected graphs only, on by default there; BC_ERR_ARG on a
+ *                     directed graph): update the dependency row of a source s with
+ *                     at most 32 changed pairs (s,t) by adding delta'_st(x) - delta_st(x)
+ *                     for those pairs (the pair dependencies of Section 2; pairs whose
+ *                     distance and path count did not change keep their shortest paths
+ *                     and hence their dependencies) instead of re-running Algorithm 1
+ *                     for s.  Off: every changed source is re-accumulated (Section 5).
+ *                     The two give the same D and sigma bit for bit and dependencies
+ *                     within rounding.
  */
 int bc_set_option(bc_graph* g, const char* name, int64_t value);
 
@@ -314,7 +328,8 @@ int bc_get_edges(bc_graph* g, int64_t* m, int32_t* src, int32_t* dst, int64_t* w
  * order; whenever a graph has nothing on the device, all its queued requests are
  * launched together on its own stream (continuous batching), so requests that arrive
  * while it is busy join its next launch and different graphs' launches overlap.  A
- * graph's device state (about n^2 * (distance bytes + 16) bytes) is built only when
+ * graph's device state (about n^2 * (distance bytes + 16) bytes, twice the distance
+ * bytes + 24 for undirected graphs, which keep rows saved for pair corrections) is built only when
  * the budget and the device's free memory leave room; when a graph with queued
  * requests needs room, idle graphs are evicted least-recently-used first and rebuilt
  * from their current edges when needed again.  Results are the same as applying each

@@ -44,7 +44,8 @@ EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "
            "bc_batch_last_ms", "bc_batch_last_error", "bc_batch_destroy", "bc_get_edges",
            "bc_server_create", "bc_server_add_graph", "bc_server_submit", "bc_server_poll",
            "bc_server_pending", "bc_server_graph", "bc_server_stats", "bc_server_destroy"]
-PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping"]
+PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping", "snapshot",
+                   "pair_corrections"]
 
 
 class bc_info(ctypes.Structure):
@@ -54,7 +55,9 @@ class bc_info(ctypes.Structure):
                 ("noop_updates", ctypes.c_int64), ("max_rows", ctypes.c_int64),
                 ("rows_scanned", ctypes.c_int64), ("pairs_lowered", ctypes.c_int64),
                 ("pairs_tied", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double)]
+                ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double),
+                ("rows_full", ctypes.c_int64), ("estar_rebuilds", ctypes.c_int64),
+                ("estar_moves", ctypes.c_int64)]
 
 
 RESULT_DTYPE = np.dtype([("request_id", "<i8"), ("graph_id", "<i4"), ("status", "<i4"),

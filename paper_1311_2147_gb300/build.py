@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbcgpu.so")
-SOURCES = ["bc_api.cu", "k_update.cu", "k_accum.cu", "k_static.cu", "k_noalloc.cu", "k_batch.cu", "bc_server.cu"]
+SOURCES = ["bc_api.cu", "k_update.cu", "k_accum.cu", "k_pair.cu", "k_static.cu", "k_noalloc.cu", "k_batch.cu",
+           "bc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

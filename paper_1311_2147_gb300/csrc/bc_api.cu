@@ -40,7 +40,14 @@ struct bc_graph {
     // weights of every arc of G (G_D for undirected graphs)
     std::unordered_map<uint64_t, int64_t> wmap;
     // host mirror of the E* superset CSR
+    // (slots [0, pool_top) hold the laid-out segments and moved ones; a vertex whose
+    // segment fills up is moved to pool_top with room to grow, and E* is laid out
+    // again only when the free region runs out)
     std::vector<int32_t> e_off, e_len, e_src, e_dst;
+    std::vector<int32_t> e_capv;          // slots of each vertex's segment
+    int64_t pool_top = 0;
+    int64_t estar_rebuilds = 0;
+    int64_t estar_moves = 0;
     std::vector<int64_t> e_w;
     std::unordered_map<uint64_t, int32_t> eslot;
     int64_t estar_arcs = 0;
@@ -56,7 +63,6 @@ struct bc_graph {
     int64_t* h_stats = nullptr;           // pinned
     uint8_t* d_keep = nullptr;
     int64_t d_keep_cap = 0;
-    int64_t big_cap = 0;
     int64_t ws_cap = 0;
     cudaEvent_t ev_done = nullptr;
     int64_t bytes = 0;
@@ -180,34 +186,23 @@ int sync_check(bc_graph* g) {
     return BC_OK;
 }
 
-// Lay the E* superset out with slack per vertex and upload it.
+// Lay the E* superset out with slack per vertex and upload it.  The device arrays get
+// a quarter more slots than the layout needs: the free region where full segments move.
 int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<int32_t>* extra = nullptr) {
     const int32_t n = g->n;
     std::vector<int32_t> deg(n, 0);
     for (const HArc& x : arcs) deg[x.a]++;
     g->e_off.assign(n + 1, 0);
     g->e_len.assign(n, 0);
-    for (int32_t a = 0; a < n; ++a)
-        g->e_off[a + 1] = g->e_off[a] + deg[a] + 2 + deg[a] / 8 + (extra ? (*extra)[a] : 0);
-    const int64_t cap = g->e_off[n];
-    g->e_src.assign(cap, 0);
-    g->e_dst.assign(cap, -1);
-    g->e_w.assign(cap, 0);
-    g->eslot.clear();
-    g->eslot.reserve(arcs.size() * 2 + 16);
-    for (const HArc& x : arcs) {
-        const int32_t slot = g->e_off[x.a] + g->e_len[x.a]++;
-        g->e_src[slot] = x.a;
-        g->e_dst[slot] = x.b;
-        g->e_w[slot] = x.w;
-        g->eslot[arc_key(x.a, x.b)] = slot;
+    g->e_capv.assign(n, 0);
+    for (int32_t a = 0; a < n; ++a) {
+        g->e_capv[a] = deg[a] + 2 + deg[a] / 8 + (extra ? (*extra)[a] : 0);
+        g->e_off[a + 1] = g->e_off[a] + g->e_capv[a];
     }
-    for (int32_t a = 0; a < n; ++a)
-        for (int32_t s = g->e_off[a]; s < g->e_off[a + 1]; ++s) g->e_src[s] = a;
-    g->estar_arcs = (int64_t)arcs.size();
+    const int64_t cap = g->e_off[n];
     Dev& d = g->d;
     const size_t asz = g->dbytes == 4 ? sizeof(Arc<int32_t>) : sizeof(Arc<int64_t>);
-    if (cap > d.e_cap) {
+    if (cap + cap / 8 > d.e_cap) {
         dfree(g, d.e_src);
         dfree(g, d.e_arc);
         d.e_src = nullptr;
@@ -220,37 +215,33 @@ int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<i
         d.e_arc = p;
         d.e_cap = ncap;
     }
-    // vertices whose segments are walked by a whole warp
-    std::vector<int32_t> big;
+    g->pool_top = cap;
+    g->e_src.assign(d.e_cap, 0);
+    g->e_dst.assign(d.e_cap, -1);
+    g->e_w.assign(d.e_cap, 0);
+    g->eslot.clear();
+    g->eslot.reserve(arcs.size() * 2 + 16);
     for (int32_t a = 0; a < n; ++a)
-        if (g->e_off[a + 1] - g->e_off[a] > kSmallDeg) big.push_back(a);
-    if ((int64_t)big.size() > g->big_cap) {
-        dfree(g, d.e_big);
-        d.e_big = nullptr;
-        int rc;
-        if ((rc = dalloc(g, &d.e_big, big.size()))) return rc;
-        g->big_cap = (int64_t)big.size();
+        for (int32_t s = g->e_off[a]; s < g->e_off[a + 1]; ++s) g->e_src[s] = a;
+    for (const HArc& x : arcs) {
+        const int32_t slot = g->e_off[x.a] + g->e_len[x.a]++;
+        g->e_dst[slot] = x.b;
+        g->e_w[slot] = x.w;
+        g->eslot[arc_key(x.a, x.b)] = slot;
     }
-    d.e_nbig = (int32_t)big.size();
-    // free slots beyond the layout stay empty (dst = -1)
-    std::vector<int32_t> src_full(d.e_cap, 0);
-    std::copy(g->e_src.begin(), g->e_src.end(), src_full.begin());
+    g->estar_arcs = (int64_t)arcs.size();
     std::vector<unsigned char> arc_bytes(d.e_cap * asz);
     if (g->dbytes == 4) {
         Arc<int32_t>* A = reinterpret_cast<Arc<int32_t>*>(arc_bytes.data());
-        for (int64_t i = 0; i < d.e_cap; ++i)
-            A[i] = i < cap ? Arc<int32_t>{g->e_dst[i], (int32_t)g->e_w[i]} : Arc<int32_t>{-1, 0};
+        for (int64_t i = 0; i < d.e_cap; ++i) A[i] = Arc<int32_t>{g->e_dst[i], (int32_t)g->e_w[i]};
     } else {
         Arc<int64_t>* A = reinterpret_cast<Arc<int64_t>*>(arc_bytes.data());
-        for (int64_t i = 0; i < d.e_cap; ++i)
-            A[i] = i < cap ? Arc<int64_t>{(int64_t)g->e_dst[i], g->e_w[i]} : Arc<int64_t>{-1, 0};
+        for (int64_t i = 0; i < d.e_cap; ++i) A[i] = Arc<int64_t>{(int64_t)g->e_dst[i], g->e_w[i]};
     }
     CK(g, cudaMemcpyAsync(d.e_off, g->e_off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, d.st));
     CK(g, cudaMemcpyAsync(d.e_len, g->e_len.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, d.st));
-    CK(g, cudaMemcpyAsync(d.e_src, src_full.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
+    CK(g, cudaMemcpyAsync(d.e_src, g->e_src.data(), sizeof(int32_t) * d.e_cap, cudaMemcpyHostToDevice, d.st));
     CK(g, cudaMemcpyAsync(d.e_arc, arc_bytes.data(), arc_bytes.size(), cudaMemcpyHostToDevice, d.st));
-    if (!big.empty())
-        CK(g, cudaMemcpyAsync(d.e_big, big.data(), sizeof(int32_t) * big.size(), cudaMemcpyHostToDevice, d.st));
     CK(g, cudaStreamSynchronize(d.st));
     // launch shape of the accumulation depends on the capacity: size its work space
     accum_config(d);
@@ -292,6 +283,7 @@ int estar_rebuild(bc_graph* g, const std::vector<HArc>& pending) {
         arcs.push_back({g->e_src[s], g->e_dst[s], g->e_w[s]});
     }
     for (const HArc& x : pending) arcs.push_back(x);
+    g->estar_rebuilds++;
     return estar_layout(g, arcs);
 }
 
@@ -335,10 +327,33 @@ int validate_update(bc_graph* g, const bc_update& u, const bc_vedge* edges, int6
     return BC_OK;
 }
 
+// Move the segment of vertex a to the free region with room for want arcs (host mirror
+// and a device move record).  False when the free region is too small.
+bool estar_move(bc_graph* g, int32_t a, int32_t want, std::vector<EMove>& moves) {
+    const int32_t len = g->e_len[a];
+    const int64_t c = (int64_t)want + want / 2 + 8;
+    if (g->pool_top + c > g->d.e_cap) return false;
+    const int32_t from = g->e_off[a], to = (int32_t)g->pool_top;
+    g->pool_top += c;
+    for (int32_t i = 0; i < len; ++i) {
+        g->e_dst[to + i] = g->e_dst[from + i];
+        g->e_w[to + i] = g->e_w[from + i];
+        g->eslot[arc_key(a, g->e_dst[to + i])] = to + i;
+        g->e_dst[from + i] = -1;
+    }
+    for (int64_t i = 0; i < c; ++i) g->e_src[to + i] = a;
+    g->e_off[a] = to;
+    g->e_capv[a] = (int32_t)c;
+    moves.push_back({a, from, to, len});
+    g->estar_moves++;
+    return true;
+}
+
 // Apply a validated update to the host weights and the E* superset mirror; fills the
-// device writes to make.  Sets *rebuild when a vertex has no free slot left.
+// device moves and writes to make.  Sets *rebuild when a vertex has no room left and
+// the free region cannot take its segment either.
 void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::vector<EOp>& ops,
-                   std::vector<HArc>& arcs, bool* rebuild) {
+                   std::vector<EMove>& moves, std::vector<HArc>& arcs, bool* rebuild) {
     arcs.clear();
     for (const VEdge& e : ent) {
         if (!g->directed) {
@@ -352,8 +367,28 @@ void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::v
     }
     *rebuild = false;
     ops.clear();
+    moves.clear();
+    // room first: segments that cannot take their new arcs move before any slot is written
+    std::vector<std::pair<int32_t, int32_t>> need;   // (vertex, new arcs)
+    for (const HArc& x : arcs) {
+        if (g->eslot.count(arc_key(x.a, x.b))) continue;
+        auto it = std::find_if(need.begin(), need.end(), [&](const std::pair<int32_t, int32_t>& p) {
+            return p.first == x.a;
+        });
+        if (it == need.end()) need.push_back({x.a, 1});
+        else it->second++;
+    }
+    for (const auto& p : need) {
+        const int32_t a = p.first;
+        if (g->e_len[a] + p.second <= g->e_capv[a]) continue;
+        if (!estar_move(g, a, g->e_len[a] + p.second, moves)) {
+            *rebuild = true;
+            break;
+        }
+    }
     for (const HArc& x : arcs) {
         g->wmap[arc_key(x.a, x.b)] = x.w;
+        if (*rebuild) continue;
         auto it = g->eslot.find(arc_key(x.a, x.b));
         if (it != g->eslot.end()) {
             g->e_w[it->second] = x.w;
@@ -361,10 +396,6 @@ void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::v
             continue;
         }
         const int32_t a = x.a;
-        if (g->e_off[a] + g->e_len[a] >= g->e_off[a + 1]) {
-            *rebuild = true;
-            continue;
-        }
         const int32_t slot = g->e_off[a] + g->e_len[a]++;
         g->e_src[slot] = a;
         g->e_dst[slot] = x.b;
@@ -378,9 +409,18 @@ void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::v
 int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const VEdge* d_ent) {
     Dev& d = g->d;
     std::vector<EOp> ops;
+    std::vector<EMove> moves;
     std::vector<HArc> arcs;
     bool rebuild = false;
-    mirror_update(g, v, ent, ops, arcs, &rebuild);
+    mirror_update(g, v, ent, ops, moves, arcs, &rebuild);
+    // moves made before a rebuild was found necessary are applied too: the rebuild reads
+    // the device slots against the host mirror
+    for (size_t i = 0; i < moves.size(); i += kMaxEMoves) {
+        EMoves pack{};
+        pack.count = (int32_t)std::min<size_t>(kMaxEMoves, moves.size() - i);
+        for (int j = 0; j < pack.count; ++j) pack.mv[j] = moves[i + j];
+        timed(g, 4, 1, [&] { launch_estar_move(d, pack); });
+    }
     if (rebuild) {
         int rc = estar_rebuild(g, arcs);
         if (rc) return rc;
@@ -399,9 +439,11 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
     }
     const int32_t k = (int32_t)ent.size();
     const int full = g->full_scan ? 1 : 0;
+    const bool pair = d.pair_on != 0;
     if (kin) {
         timed(g, 3, 1, [&] { launch_alg4_in(d, v, d_ent, k); });
         timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
+        if (pair) timed(g, 5, 1, [&] { launch_snapshot(d, d.rows, d.counts, -1); });
         timed(g, 0, 1, [&] { launch_scan_in(d, v); });
     }
     if (kout) {
@@ -410,13 +452,29 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             launch_rows_out(d, v, d_ent, k);
         });
         timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
+        if (pair) timed(g, 5, 1, [&] { launch_snapshot(d, d.rows, d.counts, v); });
         timed(g, 0, 1, [&] { launch_scan_out(d, v); });
         timed(g, 3, 1, [&] { launch_write_row(d, v); });
     }
-    timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
-    timed(g, 2, 2, [&] { launch_bc_rows(d, -1, 0); });
-    timed(g, 1, 1, [&] { launch_accum(d, 0); });
-    timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
+    if (pair) {
+        // rows with more changed targets than kPairCap (and row v): Algorithm 1 in full;
+        // the others: pair corrections of their dependency rows
+        timed(g, 4, 2, [&] {
+            launch_full_flags(d);
+            launch_compact(d, d.mark, 1, d.full_rows, d.counts + 3, 0, 0);
+        });
+        timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
+        timed(g, 2, 2, [&] { launch_bc_rows(d, -1, 0); });
+        timed(g, 6, 1, [&] { launch_pairdep(d); });
+        timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
+        timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
+        timed(g, 4, 1, [&] { launch_pair_clear(d); });
+    } else {
+        timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
+        timed(g, 2, 2, [&] { launch_bc_rows(d, -1, 0); });
+        timed(g, 1, 1, [&] { launch_accum(d, 0); });
+        timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
+    }
     CK(g, cudaGetLastError());
     return BC_OK;
 }
@@ -546,6 +604,19 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         destroy_all(g);
         return fail(nullptr, rc, "device allocation failed");
     }
+    // pair corrections (undirected graphs): saved rows, target lists, per-row flags
+    d.tcap = kPairCap;
+    if (!dir) {
+        uint8_t* psD = nullptr;
+        if ((rc = dalloc(g, &psD, nn * (size_t)g->dbytes)) || (rc = dalloc(g, &d.snapS, nn)) ||
+            (rc = dalloc(g, &d.snapped, n)) || (rc = dalloc(g, &d.tcnt, n)) ||
+            (rc = dalloc(g, &d.tlist, (size_t)n * kPairCap)) || (rc = dalloc(g, &d.full_rows, n))) {
+            destroy_all(g);
+            return fail(nullptr, rc, "device allocation failed");
+        }
+        d.snapD = psD;
+        d.pair_on = 1;
+    }
     if (cudaMallocHost(&g->h_err, sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost(&g->h_stats, 8 * sizeof(int64_t)) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess) {
@@ -573,6 +644,10 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     CKI(cudaMemsetAsync(d.mark, 0, n, d.st));
     CKI(cudaMemsetAsync(d.changed, 0, n, d.st));
     CKI(cudaMemsetAsync(d.counts, 0, 4 * sizeof(int32_t), d.st));
+    if (!dir) {
+        CKI(cudaMemsetAsync(d.snapped, 0, n, d.st));
+        CKI(cudaMemsetAsync(d.tcnt, 0, sizeof(int32_t) * n, d.st));
+    }
     CKI(cudaStreamSynchronize(d.st));
     CKI(cudaEventRecord(e0, d.st));
     CKI(cudaMemcpyAsync(d.g_off, off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, d.st));
@@ -828,6 +903,9 @@ int bc_get_info(bc_graph* g, bc_info* out) {
     out->pairs_lowered = g->h_stats[4];
     out->pairs_tied = g->h_stats[5];
     out->rows_scanned = g->h_stats[6];
+    out->rows_full = g->h_stats[7];
+    out->estar_rebuilds = g->estar_rebuilds;
+    out->estar_moves = g->estar_moves;
     out->kernel_launches = g->launches;
     out->state_bytes = g->bytes;
     out->last_init_ms = g->last_init_ms;
@@ -842,6 +920,11 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
     }
     if (std::strcmp(name, "profile") == 0) {
         g->profile = value != 0;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "pair_updates") == 0) {
+        if (value != 0 && g->directed) return fail(g, BC_ERR_ARG, "pair_updates needs an undirected graph");
+        g->d.pair_on = value != 0 ? 1 : 0;
         return BC_OK;
     }
     return fail(g, BC_ERR_ARG, std::string("unknown option ") + name);
@@ -1076,7 +1159,7 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
         base += n_updates[g];
         bool short_slack = false;
         for (int32_t a = 0; a < gr->n && !short_slack; ++a)
-            if (need[a] > gr->e_off[a + 1] - gr->e_off[a] - gr->e_len[a]) short_slack = true;
+            if (need[a] > gr->e_capv[a] - gr->e_len[a]) short_slack = true;
         if (short_slack) {
             std::vector<HArc> arcs;
             for (size_t s2 = 0; s2 < gr->e_dst.size(); ++s2)
@@ -1100,10 +1183,11 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
             bc_graph* gr = b->graphs[g];
             const std::vector<VEdge>& ent = ents[g][r];
             std::vector<EOp> ops;
+            std::vector<EMove> moves;
             std::vector<HArc> arcs;
             bool rebuild = false;
-            mirror_update(gr, vtx[g][r], ent, ops, arcs, &rebuild);
-            if (rebuild) return bfail(b, BC_ERR_CUDA, "internal: E* slack sized too small");
+            mirror_update(gr, vtx[g][r], ent, ops, moves, arcs, &rebuild);
+            if (rebuild || !moves.empty()) return bfail(b, BC_ERR_CUDA, "internal: E* slack sized too small");
             u.v = vtx[g][r];
             u.k = (int32_t)ent.size();
             u.present = 1;

@@ -11,11 +11,10 @@
 // E* superset ("E*+") -- every arc that lies on some shortest path, plus arcs that
 // may no longer do so (Section 6: any superset of E* gives the right DAGs) -- is a
 // CSR with per-vertex slack: arcs of vertex a sit in slots [off[a], off[a]+len[a]),
-// the slots up to off[a+1] are free (dst = -1).  Each slot is a packed (dst, w) pair
-// (Arc<DT>: 8 bytes for int32 distances, 16 for int64) so one load brings both;
-// src[] repeats the tail of each slot for passes that run over the slots.  Vertices
-// whose segment holds more than kSmallDeg slots are listed in big[] (warp-cooperative
-// handling in the accumulation).
+// followed by free slots (dst = -1).  A segment that fills up moves to the free region
+// past the laid-out ones (off[a] changes, its old slots are emptied).  Each slot is a
+// packed (dst, w) pair (Arc<DT>: 8 bytes for int32 distances, 16 for int64) so one load
+// brings both; src[] repeats the tail of each slot for passes that run over the slots.
 #pragma once
 
 #include <cstdint>
@@ -75,7 +74,7 @@ template <typename DT> struct Arc;
 template <> struct __align__(8) Arc<int32_t> { int32_t dst; int32_t w; };
 template <> struct __align__(16) Arc<int64_t> { int64_t dst; int64_t w; };
 
-constexpr int kSmallDeg = 32;   // segments up to this many slots are walked by one thread
+constexpr int kPairCap = 32;    // changed targets of a row corrected pair by pair (k_pair.cu)
 
 // One edge of a vertex update, as staged on the device (matches bc_vedge).
 struct VEdge {
@@ -97,6 +96,20 @@ struct EOps {
     int32_t count;
     int32_t pad;
     EOp op[kMaxEOps];
+};
+// Move of the E* segment of vertex a (len arcs) from slot from to slot to, in the free
+// region past the laid-out segments.
+struct EMove {
+    int32_t a;
+    int32_t from;
+    int32_t to;
+    int32_t len;
+};
+constexpr int kMaxEMoves = 32;
+struct EMoves {
+    int32_t count;
+    int32_t pad;
+    EMove mv[kMaxEMoves];
 };
 
 // Device state of one handle (plain pointers; owned by the host-side bc_graph).
@@ -122,8 +135,6 @@ struct Dev {
     int32_t* e_src;
     void* e_arc;         // Arc<DT>[e_cap]
     int64_t e_cap;
-    int32_t* e_big;      // vertices with more than kSmallDeg slots
-    int32_t e_nbig;
     // error word, counters
     int32_t* err;
     int64_t* stats;      // [0] rows re-accumulated [1] no-op updates [2] max rows [3] updates
@@ -147,6 +158,16 @@ struct Dev {
     int32_t acc_mask_smem;  // 1: the DAG slot mask lives in shared memory
     int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
     int64_t ws_stride;
+    // pair-dependency corrections (undirected graphs): rows as they were before the
+    // update, and the targets whose pair changed in each row
+    int32_t pair_on;
+    int32_t tcap;        // targets recorded per row (kPairCap); more -> full re-accumulation
+    void* snapD;         // [n*n] distance rows saved before their first change (DT)
+    uint64_t* snapS;     // [n*n] path-count rows saved likewise
+    uint8_t* snapped;    // [n] row saved in this update
+    int32_t* tcnt;       // [n] changed targets recorded for the row
+    int32_t* tlist;      // [n * tcap]
+    int32_t* full_rows;  // [n] rows re-accumulated in full (counts[3])
     cudaStream_t st;
 };
 
@@ -159,6 +180,7 @@ void accum_config(Dev& d);
 
 // ---- launches (k_update.cu) ----
 void launch_estar_write(const Dev& d, const EOps& ops);
+void launch_estar_move(const Dev& d, const EMoves& moves);
 void launch_alg4_in(const Dev& d, int32_t v, const VEdge* e, int32_t k);
 void launch_rows_out(const Dev& d, int32_t v, const VEdge* e, int32_t k);
 void launch_alg4_out(const Dev& d, int32_t v, const VEdge* e, int32_t k);
@@ -168,9 +190,14 @@ void launch_scan_in(const Dev& d, int32_t v);
 void launch_scan_out(const Dev& d, int32_t v);
 void launch_write_row(const Dev& d, int32_t v);
 void launch_estar_keep(const Dev& d, uint8_t* keep);
+void launch_snapshot(const Dev& d, const int32_t* rows, const int32_t* count, int32_t extra_row);
+void launch_full_flags(const Dev& d);
+void launch_pairdep(const Dev& d);
+void launch_pair_clear(const Dev& d);
 
 // ---- launches (k_accum.cu) ----
 void launch_accum(const Dev& d, int is_static);
+void launch_accum_rows(const Dev& d, const int32_t* rows, const int32_t* count);
 void launch_bc_rows(const Dev& d, int sign, int is_static);
 
 // ---- launches (k_static.cu) ----

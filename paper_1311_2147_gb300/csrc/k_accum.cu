@@ -14,10 +14,11 @@
 //   * delta_s. is pulled in reverse level order (Eq. 4), in float-float (ff.cuh):
 //         delta(a) = sum over DAG out-arcs (a,b) of sigma_sa / sigma_sb * (1 + delta(b))
 //                  = sigma_sa * sum over the same arcs of rho(b),
-//     with rho(b) = (1 + delta(b)) / sigma_sb kept per vertex.  Each vertex is summed by
-//     a group of kGroup lanes (segments of at most kSmallDeg slots) or by a warp (longer
-//     segments), each lane over a fixed stride of slots and a fixed butterfly across
-//     the lanes, so the result does not depend on scheduling.
+//     with rho(b) = (1 + delta(b)) / sigma_sb kept per vertex.  The DAG out-arcs of a
+//     level are flattened over the CTA (a block scan of the per-vertex arc counts, each
+//     thread fetching rho of one arc, each vertex summing its own arcs in slot order);
+//     vertices with more than kBigDag DAG out-arcs are summed by a warp over a fixed
+//     stride and butterfly.  Either way the result does not depend on scheduling.
 // The kernel stages in shared memory the source's distance row (16-bit when every
 // finite distance of the row is below 65535, otherwise read from its row of D), the
 // packed 16-bit Kahn counters, the 16-bit level order and a bit mask over the slots of
@@ -66,7 +67,7 @@ __global__ void k_bc_finish(int n, const int32_t* rows, const int32_t* count, co
 // ------------------------------------------------------------------ launches
 
 template <typename DT>
-static AccArgs<DT> acc_args(const Dev& d) {
+static AccArgs<DT> acc_args(const Dev& d, const int32_t* rows, const int32_t* count) {
     AccArgs<DT> a;
     a.n = d.n;
     a.D = (const DT*)d.D;
@@ -77,10 +78,8 @@ static AccArgs<DT> acc_args(const Dev& d) {
     a.e_src = d.e_src;
     a.e_arc = (const Arc<DT>*)d.e_arc;
     a.e_cap = d.e_cap;
-    a.e_big = d.e_big;
-    a.e_nbig = d.e_nbig;
-    a.rows = d.acc_rows;
-    a.count = d.counts + 1;
+    a.rows = rows;
+    a.count = count;
     a.ws = d.ws;
     a.ws_stride = d.ws_stride;
     a.err = d.err;
@@ -122,17 +121,22 @@ void accum_config(Dev& d) {
     d.ws_stride = head + (in_smem ? 0 : (((int64_t)mb / 4 + 3) & ~(int64_t)3));
 }
 
-void launch_accum(const Dev& d, int is_static) {
+// Algorithm 1 for the sources listed in rows[0..*count), or for every source.
+static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
     const int grid = d.acc_grid;
     const size_t smem = (size_t)d.acc_smem;
     if (d.dbytes == 4) {
-        if (is_static) k_accum_smem<int32_t, true><<<grid, kAccThreads, smem, d.st>>>(acc_args<int32_t>(d));
-        else k_accum_smem<int32_t, false><<<grid, kAccThreads, smem, d.st>>>(acc_args<int32_t>(d));
+        if (is_static) k_accum_smem<int32_t, true><<<grid, kAccThreads, smem, d.st>>>(acc_args<int32_t>(d, rows, count));
+        else k_accum_smem<int32_t, false><<<grid, kAccThreads, smem, d.st>>>(acc_args<int32_t>(d, rows, count));
     } else {
-        if (is_static) k_accum_smem<int64_t, true><<<grid, kAccThreads, smem, d.st>>>(acc_args<int64_t>(d));
-        else k_accum_smem<int64_t, false><<<grid, kAccThreads, smem, d.st>>>(acc_args<int64_t>(d));
+        if (is_static) k_accum_smem<int64_t, true><<<grid, kAccThreads, smem, d.st>>>(acc_args<int64_t>(d, rows, count));
+        else k_accum_smem<int64_t, false><<<grid, kAccThreads, smem, d.st>>>(acc_args<int64_t>(d, rows, count));
     }
 }
+
+void launch_accum(const Dev& d, int is_static) { accum(d, is_static, d.acc_rows, d.counts + 1); }
+
+void launch_accum_rows(const Dev& d, const int32_t* rows, const int32_t* count) { accum(d, 0, rows, count); }
 
 // sign = -1 / +1: subtract / add the rows listed in acc_rows; is_static: all rows,
 // overwriting BC.

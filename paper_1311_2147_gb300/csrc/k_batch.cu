@@ -174,6 +174,9 @@ __device__ __forceinline__ ScanArgs<DT> batch_scan_args(const Dev& d, const Batc
     a.fM = d.fM;
     a.err = d.err;
     a.stats = d.stats;
+    a.tcnt = nullptr;   // the batched path re-accumulates every changed row
+    a.tlist = nullptr;
+    a.tcap = 0;
     if (phase == 0) {
         a.cD = (const DT*)d.D + (size_t)u.v * d.n;
         a.cS = d.S + (size_t)u.v * d.n;
@@ -290,8 +293,6 @@ __global__ void __launch_bounds__(kAccThreads) kb_accum(BatchArgs b, int r, cons
         a.e_src = d.e_src;
         a.e_arc = (const Arc<DT>*)d.e_arc;
         a.e_cap = d.e_cap;
-        a.e_big = d.e_big;
-        a.e_nbig = d.e_nbig;
         a.rows = d.acc_rows;
         a.count = d.counts + 1;
         a.ws = b.ws;

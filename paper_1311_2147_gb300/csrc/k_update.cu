@@ -35,6 +35,20 @@ __global__ void k_estar_write(int32_t* e_src, void* e_arc, int32_t* e_len, int d
     atomicMax(e_len + o.a, o.len_a);   // lengths only grow between rebuilds
 }
 
+// One CTA per move: copy the segment, empty its old slots, point e_off[a] at the copy.
+// Source and destination ranges of all moves are disjoint.
+template <typename DT>
+__global__ void k_estar_move(int32_t* e_off, int32_t* e_src, Arc<DT>* e_arc, EMoves moves) {
+    if ((int)blockIdx.x >= moves.count) return;
+    const EMove m = moves.mv[blockIdx.x];
+    for (int i = threadIdx.x; i < m.len; i += blockDim.x) {
+        e_arc[m.to + i] = e_arc[m.from + i];
+        e_src[m.to + i] = m.a;
+        e_arc[m.from + i].dst = -1;
+    }
+    if (threadIdx.x == 0) e_off[m.a] = m.to;
+}
+
 template <typename DT>
 __global__ void k_alg4_in(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
                           int v, const VEdge* __restrict__ e, int k, int directed,
@@ -138,6 +152,14 @@ void launch_estar_write(const Dev& d, const EOps& ops) {
     k_estar_write<<<1, kMaxEOps, 0, d.st>>>(d.e_src, d.e_arc, d.e_len, d.dbytes, ops);
 }
 
+void launch_estar_move(const Dev& d, const EMoves& moves) {
+    if (moves.count <= 0) return;
+    if (d.dbytes == 4)
+        k_estar_move<int32_t><<<moves.count, 128, 0, d.st>>>(d.e_off, d.e_src, (Arc<int32_t>*)d.e_arc, moves);
+    else
+        k_estar_move<int64_t><<<moves.count, 128, 0, d.st>>>(d.e_off, d.e_src, (Arc<int64_t>*)d.e_arc, moves);
+}
+
 void launch_alg4_in(const Dev& d, int32_t v, const VEdge* e, int32_t k) {
     if (d.dbytes == 4)
         k_alg4_in<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
@@ -201,6 +223,9 @@ static ScanArgs<DT> scan_args(const Dev& d) {
     a.skip_row = -1;
     a.err = d.err;
     a.stats = d.stats;
+    a.tcnt = d.pair_on ? d.tcnt : nullptr;
+    a.tlist = d.tlist;
+    a.tcap = d.tcap;
     return a;
 }
 

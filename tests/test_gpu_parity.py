@@ -156,6 +156,36 @@ def test_batch_of_updates_matches_one_by_one():
     compare_full(a, synth.apply_updates(g, ups))
 
 
+def test_estar_segment_moves_and_rebuilds():
+    # vertex updates with many new edges at low-degree vertices overflow their E*
+    # segments: the segments move to the free region, and once that is used up E* is
+    # laid out again; results must not depend on either
+    for directed in (False, True):
+        g = synth.path_graph(160, directed, 3)
+        em = synth.EdgeMap.of(g)
+        rng = synth.Rng(44 + directed)
+        ups = []
+        for i in range(14):
+            v = int(rng.below(g.n, 1)[0])
+            nb = [int(x) for x in rng.below(g.n, 24) if int(x) != v]
+            seen, edges = set(), []
+            d = i % 2 if directed else 0
+            for x in nb:
+                exists = em.get(x, v) if d == 0 else em.get(v, x)
+                if x in seen or exists is not None:
+                    continue
+                seen.add(x)
+                edges.append((x, 1 + (x + v) % 5, d))
+                if len(edges) == 16:
+                    break
+            up = ("vertex", v, edges)
+            synth.apply_update(em, up)
+            ups.append(up)
+        bg = _stream_check(g, ups, "i32", every=3, label=f"E* moves directed={directed}")
+        info = bg.bc_get_info()
+        assert info["estar_moves"] > 0 and info["estar_rebuilds"] > 0, info
+
+
 # ------------------------------------------------------------------ invariants
 
 def test_lemma1_column_u_row_v_unchanged():
