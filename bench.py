@@ -505,9 +505,10 @@ def run_serve(args):
 
 def run_ncu_case(args):
     """A small case of one kernel class for ncu captures (a few GB on the device at most):
-    BA n=8192 (state 1.3 GB, above L2), static init, then either two vertex updates
-    (accumulation and BC rows) or one edge update with the rank-1 pass over every row
-    (the paper's all-pairs Step 2)."""
+    BA n=8192 (state 2.1 GB, above L2), static init, then either two vertex updates with
+    every changed row re-accumulated (accumulation and BC rows), the first four updates
+    of the stream with pair corrections (pair), or two edge updates with the rank-1
+    pass over every row (the paper's all-pairs Step 2)."""
     from paper_1311_2147_gb300 import binding, synth
     binding.load()
     g, ups = synth.workload_ba16384(n=args.ncu_n, n_updates=64)
@@ -515,7 +516,10 @@ def run_ncu_case(args):
     if args.ncu_case == "scan":
         bg.bc_set_option("full_scan", 1)
         sel = [u for u in ups if u[0] == "edge"][:2]
+    elif args.ncu_case == "pair":
+        sel = ups[:4]
     else:
+        bg.bc_set_option("pair_updates", 0)
         sel = [u for u in ups if u[0] == "vertex"][:2]
     per_update = []
     for u in sel:
@@ -523,7 +527,7 @@ def run_ncu_case(args):
         rc, _ = bg.bc_apply_updates([u])
         assert rc == 0, bg.last_error()
         after = bg.bc_get_info()
-        per_update.append({k: after[k] - before[k] for k in ("rows_reaccumulated", "rows_scanned",
+        per_update.append({k: after[k] - before[k] for k in ("rows_reaccumulated", "rows_full", "rows_scanned",
                                                              "pairs_lowered", "pairs_tied")})
     print(json.dumps({"ncu_case": args.ncu_case, "n": g.n, "per_update": per_update, "info": bg.bc_get_info()}))
     return 0
@@ -546,7 +550,7 @@ def main():
     ap.add_argument("--recompute-runs", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
-    ap.add_argument("--ncu-case", choices=["accumulate", "scan"], default=None,
+    ap.add_argument("--ncu-case", choices=["accumulate", "pair", "scan"], default=None,
                     help="run only a small case of one kernel class (for ncu captures)")
     ap.add_argument("--ncu-n", type=int, default=8192)
     args = ap.parse_args()

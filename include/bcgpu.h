@@ -235,7 +235,7 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
  *   "profile"   0|1: record CUDA events around every launch (see bc_get_profile).
  *   "pair_updates" 0|1 (undirected graphs only, on by default there; BC_ERR_ARG on a
  *                     directed graph): update the dependency row of a source s with
- *                     at most 32 changed pairs (s,t) by adding delta'_st(x) - delta_st(x)
+ *                     at most 128 changed pairs (s,t) by adding delta'_st(x) - delta_st(x)
  *                     for those pairs (the pair dependencies of Section 2; pairs whose
  *                     distance and path count did not change keep their shortest paths
  *                     and hence their dependencies) instead of re-running Algorithm 1

@@ -65,6 +65,9 @@ struct bc_graph {
     int64_t d_keep_cap = 0;
     int64_t ws_cap = 0;
     cudaEvent_t ev_done = nullptr;
+    // second stream: full re-accumulation of some rows runs beside the pair corrections
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t bytes = 0;
     double last_init_ms = 0.0;
     std::vector<void*> allocs;
@@ -465,8 +468,23 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
         });
         timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
         timed(g, 2, 2, [&] { launch_bc_rows(d, -1, 0); });
-        timed(g, 6, 1, [&] { launch_pairdep(d); });
-        timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
+        if (!g->profile) {
+            // the two write disjoint dependency rows and only read the rest of the state:
+            // the (latency-bound, often partial-wave) accumulation of the full rows runs
+            // on the second stream beside the pair corrections
+            Dev ds = d;
+            ds.st = g->side;
+            CK(g, cudaEventRecord(g->ev_fork, d.st));
+            CK(g, cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+            launch_accum_rows(ds, d.full_rows, d.counts + 3);
+            CK(g, cudaEventRecord(g->ev_join, g->side));
+            launch_pairdep(d);
+            CK(g, cudaStreamWaitEvent(d.st, g->ev_join, 0));
+            g->launches += 4;
+        } else {
+            timed(g, 6, 3, [&] { launch_pairdep(d); });
+            timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
+        }
         timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
         timed(g, 4, 1, [&] { launch_pair_clear(d); });
     } else {
@@ -481,7 +499,13 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
 
 void destroy_all(bc_graph* g) {
     if (!g) return;
-    if (g->d.st || true) cudaStreamSynchronize(g->d.st);
+    cudaStreamSynchronize(g->d.st);
+    if (g->side) {
+        cudaStreamSynchronize(g->side);
+        cudaStreamDestroy(g->side);
+    }
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
     for (void* p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->h_err) cudaFreeHost(g->h_err);
@@ -598,7 +622,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         (rc = dalloc(g, &d.g_dst, arcs)) || (rc = dalloc(g, &d.e_off, n + 1)) || (rc = dalloc(g, &d.e_len, n)) ||
         (rc = dalloc(g, &d.err, 1)) || (rc = dalloc(g, &d.stats, 8)) || (rc = dalloc(g, &d.mark, n)) ||
         (rc = dalloc(g, &d.changed, n)) || (rc = dalloc(g, &d.rows, n)) || (rc = dalloc(g, &d.acc_rows, n)) ||
-        (rc = dalloc(g, &d.counts, 4)) || (rc = dalloc(g, &d.fS, n)) || (rc = dalloc(g, &d.fM, n)) ||
+        (rc = dalloc(g, &d.counts, 8)) || (rc = dalloc(g, &d.fS, n)) || (rc = dalloc(g, &d.fM, n)) ||
         (rc = dalloc(g, &d.cS, n)) || (rc = dalloc(g, &d.cM, n)) ||
         (rc = dalloc(g, &d.partial, (size_t)d.nrb_max * n))) {
         destroy_all(g);
@@ -610,7 +634,9 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         uint8_t* psD = nullptr;
         if ((rc = dalloc(g, &psD, nn * (size_t)g->dbytes)) || (rc = dalloc(g, &d.snapS, nn)) ||
             (rc = dalloc(g, &d.snapped, n)) || (rc = dalloc(g, &d.tcnt, n)) ||
-            (rc = dalloc(g, &d.tlist, (size_t)n * kPairCap)) || (rc = dalloc(g, &d.full_rows, n))) {
+            (rc = dalloc(g, &d.tlist, (size_t)n * kPairCap)) || (rc = dalloc(g, &d.full_rows, n)) ||
+            (rc = dalloc(g, reinterpret_cast<uint8_t**>(&d.plan), (size_t)n * kPairCap * 40)) ||
+            (rc = dalloc(g, &d.pair_w, (size_t)n + 1))) {
             destroy_all(g);
             return fail(nullptr, rc, "device allocation failed");
         }
@@ -619,9 +645,12 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     }
     if (cudaMallocHost(&g->h_err, sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost(&g->h_stats, 8 * sizeof(int64_t)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        (!dir && (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess))) {
         destroy_all(g);
-        return fail(nullptr, BC_ERR_OOM, "pinned host allocation failed");
+        return fail(nullptr, BC_ERR_OOM, "pinned host allocation, stream or event creation failed");
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -643,7 +672,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     CKI(cudaMemsetAsync(d.stats, 0, 8 * sizeof(int64_t), d.st));
     CKI(cudaMemsetAsync(d.mark, 0, n, d.st));
     CKI(cudaMemsetAsync(d.changed, 0, n, d.st));
-    CKI(cudaMemsetAsync(d.counts, 0, 4 * sizeof(int32_t), d.st));
+    CKI(cudaMemsetAsync(d.counts, 0, 8 * sizeof(int32_t), d.st));
     if (!dir) {
         CKI(cudaMemsetAsync(d.snapped, 0, n, d.st));
         CKI(cudaMemsetAsync(d.tcnt, 0, sizeof(int32_t) * n, d.st));

@@ -74,7 +74,7 @@ template <typename DT> struct Arc;
 template <> struct __align__(8) Arc<int32_t> { int32_t dst; int32_t w; };
 template <> struct __align__(16) Arc<int64_t> { int64_t dst; int64_t w; };
 
-constexpr int kPairCap = 32;    // changed targets of a row corrected pair by pair (k_pair.cu)
+constexpr int kPairCap = 128;   // changed targets of a row corrected pair by pair (k_pair.cu)
 
 // One edge of a vertex update, as staged on the device (matches bc_vedge).
 struct VEdge {
@@ -144,7 +144,7 @@ struct Dev {
     uint8_t* changed;    // [n] rows that changed in any phase of the current update
     int32_t* rows;       // [n] compacted rows of the current phase
     int32_t* acc_rows;   // [n] compacted rows to re-accumulate
-    int32_t* counts;     // [0] phase rows [1] accumulation rows
+    int32_t* counts;     // [0] phase rows [1] accumulation rows [3] full rows
     void* fD;            // [n] per-row distance to v after the phase (DT)
     uint64_t* fS;        // [n] per-row path count to v after the phase
     uint64_t* fM;        // [n] per-row multiplier of a tie
@@ -167,6 +167,8 @@ struct Dev {
     uint8_t* snapped;    // [n] row saved in this update
     int32_t* tcnt;       // [n] changed targets recorded for the row
     int32_t* tlist;      // [n * tcap]
+    void* plan;          // [n * tcap] per-target scalars of the pair corrections (k_pair.cu)
+    int64_t* pair_w;     // [n + 1] prefix of the pair corrections' work item weights
     int32_t* full_rows;  // [n] rows re-accumulated in full (counts[3])
     cudaStream_t st;
 };

@@ -57,6 +57,40 @@ __global__ void k_bc_partial(int n, const int32_t* rows, const int32_t* count, c
     dev_bc_partial(t, blockIdx.y, n, rows, rows ? *count : n, Dl, partial);
 }
 
+// The same partial sums for two adjacent columns per thread (n even): 16-byte loads of
+// both columns' float-float values, eight rows' loads issued before they are added;
+// each column still adds its rows one by one in list order, as dev_bc_partial does, so
+// the sums are bit-identical.
+constexpr int kBcUnroll = 8;
+__global__ void __launch_bounds__(256) k_bc_partial2(int n, const int32_t* rows, const int32_t* count,
+                                                     const ff* Dl, ff* partial, const int32_t* err) {
+    if (*err) return;
+    const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int rb = blockIdx.y;
+    const int total = rows ? *count : n;
+    const int r0 = rb * kRowsPerBlock;
+    if (r0 >= total || t >= n) return;
+    const int r1 = min(total, r0 + kRowsPerBlock);
+    ff a0{0.0f, 0.0f}, a1{0.0f, 0.0f};
+    for (int r = r0; r < r1; r += kBcUnroll) {
+        int sr[kBcUnroll];
+        float4 v[kBcUnroll];
+#pragma unroll
+        for (int k = 0; k < kBcUnroll; ++k) sr[k] = r + k < r1 ? (rows ? rows[r + k] : r + k) : -1;
+#pragma unroll
+        for (int k = 0; k < kBcUnroll; ++k)
+            if (sr[k] >= 0) v[k] = __ldcs(reinterpret_cast<const float4*>(Dl + (size_t)sr[k] * n + t));
+#pragma unroll
+        for (int k = 0; k < kBcUnroll; ++k) {
+            if (sr[k] < 0) break;
+            if (sr[k] != t) a0 = ff_add(a0, ff{v[k].x, v[k].y});
+            if (sr[k] != t + 1) a1 = ff_add(a1, ff{v[k].z, v[k].w});
+        }
+    }
+    partial[(size_t)rb * n + t] = a0;
+    partial[(size_t)rb * n + t + 1] = a1;
+}
+
 __global__ void k_bc_finish(int n, const int32_t* rows, const int32_t* count, const ff* partial,
                             double sign, int overwrite, double* hi, double* lo, const int32_t* err) {
     if (*err) return;
@@ -144,7 +178,12 @@ void launch_bc_rows(const Dev& d, int sign, int is_static) {
     const int tb = (d.n + 255) / 256;
     dim3 g1(tb, d.nrb_max);
     const int32_t* rows = is_static ? nullptr : d.acc_rows;
-    k_bc_partial<<<g1, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.Dl, d.partial, d.err);
+    if (d.n % 2 == 0) {
+        dim3 g2((d.n / 2 + 255) / 256, d.nrb_max);
+        k_bc_partial2<<<g2, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.Dl, d.partial, d.err);
+    } else {
+        k_bc_partial<<<g1, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.Dl, d.partial, d.err);
+    }
     k_bc_finish<<<tb, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.partial, (double)sign, is_static,
                                       d.bc_hi, d.bc_lo, d.err);
 }

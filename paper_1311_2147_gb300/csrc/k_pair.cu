@@ -15,10 +15,13 @@
 // which k_snapshot saves before the first write to each row, and the new terms read
 // the state after both phases.  In G_D of an undirected graph d(x,t) = d(t,x) and
 // sigma_xt = sigma_tx before and after the update, so the column t of the formula is
-// row t, read contiguously.  Rows with more targets, and row v (rewritten whole by the
-// OUT phase, its targets unrecorded), are re-accumulated by Algorithm 1 instead.
+// row t, read contiguously.  Row v, which the OUT phase rewrites whole, records the
+// targets where its new values differ.  Rows with more targets than the cap are
+// re-accumulated by Algorithm 1 instead.
 #include "bc_device.cuh"
 #include "ff.cuh"
+
+static_assert(bcg::kPairCap <= 1024, "the targets of a row are sorted by one CTA");
 
 namespace bcg {
 
@@ -26,13 +29,12 @@ constexpr int kSnapThreads = 256;
 constexpr int kPairThreads = 256;
 
 // Save rows[0..count) (and row extra_row when the OUT phase changes it) before their
-// first write in this update.  A saved row of v is also sent to the full path by a
-// target count above the cap.  The rows of one launch are distinct.
+// first write in this update.  The rows of one launch are distinct.
 template <typename DT>
 __global__ void __launch_bounds__(kSnapThreads)
 k_snapshot(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S, DT* sD, uint64_t* sS,
            uint8_t* snapped, const int32_t* rows, const int32_t* count, int extra_row,
-           const uint8_t* changed, int32_t* tcnt, int tcap, const int32_t* err) {
+           const uint8_t* changed, const int32_t* err) {
     __shared__ int s_do;
     if (*err) return;
     const int cnt = *count;
@@ -41,10 +43,7 @@ k_snapshot(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S, DT* 
         const int s = i < cnt ? rows[i] : extra_row;
         if (threadIdx.x == 0) {
             int go = snapped[s] == 0;
-            if (i >= cnt) {
-                go = go && changed[s] != 0;
-                if (changed[s]) tcnt[s] = tcap + 1;
-            }
+            if (i >= cnt) go = go && changed[s] != 0;
             if (go) snapped[s] = 1;
             s_do = go;
         }
@@ -70,7 +69,7 @@ k_snapshot(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S, DT* 
     }
 }
 
-// mark[s] = row s changed and has more recorded targets than the cap (or is row v).
+// mark[s] = row s changed and has more recorded targets than the cap.
 __global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt, int tcap, uint8_t* mark) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) mark[s] = (changed[s] != 0 && tcnt[s] > tcap) ? 1 : 0;
@@ -89,6 +88,20 @@ __global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t*
     }
 }
 
+// One changed target t of a row s, as prepared by k_pair_plan: the pair's distance and
+// reciprocal path count before and after the update (-1: no path), and whether row t
+// was saved (its old values then come from the saved copy).
+struct PairTgt {
+    int32_t t;
+    int32_t snap_t;
+    int64_t dold;
+    int64_t dnew;
+    ff rold;
+    ff rnew;
+};
+
+static_assert(sizeof(PairTgt) == 40, "the plan is allocated with 40 bytes per target");
+
 template <typename DT>
 struct PairArgs {
     int n;
@@ -97,8 +110,10 @@ struct PairArgs {
     const DT* sD;           // rows saved before the update (where snapped)
     const uint64_t* sS;
     const uint8_t* snapped;
-    const int32_t* tcnt;
+    int32_t* tcnt;          // recorded targets per row; k_pair_plan replaces it by the unique count
     const int32_t* tlist;
+    PairTgt* plan;          // [n * tcap]
+    int64_t* wpre;          // [n + 1] prefix of the item weights of the listed rows
     int tcap;
     const int32_t* rows;
     const int32_t* count;
@@ -106,134 +121,280 @@ struct PairArgs {
     int32_t* err;
 };
 
+// One CTA (kPlanThreads >= tcap threads) per listed row with 1..tcap recorded targets:
+// sort them, drop repeats (a pair can change in both phases), and write the per-target
+// scalars of the plan; tcnt[s] becomes the number of distinct targets.
+constexpr int kPlanThreads = kPairCap;
+
+template <typename DT>
+__global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
+    __shared__ int32_t s_val[kPlanThreads];
+    __shared__ int s_first[kPlanThreads];
+    if (*a.err) return;
+    const int n = a.n;
+    const int64_t INF = Inf<DT>::v;
+    const int cnt = *a.count;
+    const int tid = threadIdx.x;
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int s = a.rows[i];
+        const int T = a.tcnt[s];
+        if (T == 0 || T > a.tcap) continue;   // block-uniform
+        const int val = tid < T ? a.tlist[(size_t)s * a.tcap + tid] : INT32_MAX;
+        s_val[tid] = val;
+        __syncthreads();
+        bool first = val != INT32_MAX;
+        for (int j = 0; j < tid && first; ++j) first = s_val[j] != val;
+        s_first[tid] = first;
+        __syncthreads();
+        int pos = 0;
+        for (int j = 0; j < T; ++j) pos += s_first[j] && s_val[j] < val;
+        const int U = __syncthreads_count(first);
+        if (first) {
+            const size_t rs = (size_t)s * n;
+            const bool snap_s = a.snapped[s] != 0;
+            const int t = val;
+            const int64_t dol = (snap_s ? a.sD : a.D)[rs + t], dnw = a.D[rs + t];
+            const uint64_t sol = (snap_s ? a.sS : a.S)[rs + t], snw = a.S[rs + t];
+            PairTgt p;
+            p.t = t;
+            p.snap_t = a.snapped[t] != 0;
+            p.dold = (dol == INF || sol == 0) ? -1 : dol;
+            p.dnew = (dnw == INF || snw == 0) ? -1 : dnw;
+            p.rold = sol ? ff_rcp(ff_from_u64(sol)) : ff{0.f, 0.f};
+            p.rnew = snw ? ff_rcp(ff_from_u64(snw)) : ff{0.f, 0.f};
+            a.plan[(size_t)s * a.tcap + pos] = p;
+        }
+        if (tid == 0) a.tcnt[s] = U;
+        __syncthreads();
+    }
+}
+
 // sigma_sx * sigma_xt / sigma_st in float-float (the quotient as a product with the
 // reciprocal of sigma_st).
 __device__ __forceinline__ ff pair_term(uint64_t a, uint64_t b, const ff& rcp) {
     return ff_mul(ff_mul(ff_from_u64(a), ff_from_u64(b)), rcp);
 }
 
-// Distances of VN consecutive columns (one 16-byte load when VN > 1).
+// VN consecutive distances (one 16-byte load when VN > 1).
 template <typename DT, int VN>
-__device__ __forceinline__ void load_d(const DT* p, int64_t* o) {
-    if constexpr (VN == 1) {
-        o[0] = p[0];
-    } else {
-        Vec<DT>::unpack(*reinterpret_cast<const typename Vec<DT>::T*>(p), o);
-    }
-}
-
-// Adds sign * sigma_sx sigma_xt / sigma_st to acc[q] for the columns x = x0 + q on a
-// shortest s-t path (d(s,x) + d(x,t) = d(s,t), x not in {s, t}) of one state (old or
-// new).  Row t is read only when some column can be on such a path (d(s,x) < d(s,t)).
-template <typename DT, int VN>
-__device__ __forceinline__ void pair_terms(int x0, int s, int t, int64_t dst, const ff& rcp, float sign,
-                                           const int64_t* ds, const DT* Dt, const uint64_t* St,
-                                           const uint64_t* Ss, uint64_t* ss, unsigned& have, ff* acc,
-                                           unsigned& any) {
-    bool cand = false;
-#pragma unroll
-    for (int q = 0; q < VN; ++q) cand |= ds[q] < dst;
-    if (!cand) return;
-    int64_t dt[VN];
-    load_d<DT, VN>(Dt + x0, dt);
-#pragma unroll
-    for (int q = 0; q < VN; ++q) {
-        const int x = x0 + q;
-        if (ds[q] >= dst || x == s || x == t || dt[q] == Inf<DT>::v) continue;
-        // both terms are below 2^63: their unsigned sum is exact
-        if ((uint64_t)ds[q] + (uint64_t)dt[q] != (uint64_t)dst) continue;
-        if (!((have >> q) & 1u)) {
-            ss[q] = Ss[x];
-            have |= 1u << q;
+struct DVec {
+    DT v[VN];
+    __device__ __forceinline__ void load(const DT* p) {
+        if constexpr (VN == 4) {
+            const int4 x = *reinterpret_cast<const int4*>(p);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else if constexpr (VN == 2) {
+            const longlong2 x = *reinterpret_cast<const longlong2*>(p);
+            v[0] = x.x; v[1] = x.y;
+        } else {
+            v[0] = p[0];
         }
-        const ff c = pair_term(ss[q], St[x], rcp);
-        acc[q] = ff_add(acc[q], ff{sign * c.hi, sign * c.lo});
-        any |= 1u << q;
     }
+};
+
+template <typename DT> struct Unsigned;
+template <> struct Unsigned<int32_t> { using T = uint32_t; };
+template <> struct Unsigned<int64_t> { using T = uint64_t; };
+
+// Whether some column x0+q can lie on a shortest s-t path of one state:
+// d(s,x) + d(x,t) = d(s,t).  Distances are below INF = DT max, so their unsigned sum
+// never wraps, and a sum with an INF term exceeds every finite d(s,t).  (The caller
+// replaces d(s,s) by INF; x = t, where d(x,t) = 0, is excluded by on_path.)
+template <typename DT, int VN>
+__device__ __forceinline__ bool any_sum(const DVec<DT, VN>& ds, const DVec<DT, VN>& dt, int64_t dst) {
+    using U = typename Unsigned<DT>::T;
+    bool hit = false;
+#pragma unroll
+    for (int q = 0; q < VN; ++q) hit |= (U)ds.v[q] + (U)dt.v[q] == (U)dst;
+    return hit;
 }
 
-// One CTA per listed row s with 1..tcap recorded targets.  The targets are sorted and
-// made unique by warp 0 (so the sum runs in a fixed order), then every thread takes VN
-// consecutive columns x at a time and adds sum_t [delta'_st(x) - delta_st(x)] to
-// delta_s(x).
+// Bit q set where column x0+q lies on a shortest s-t path: the sum matches and
+// d(x,t) > 0.
 template <typename DT, int VN>
-__global__ void __launch_bounds__(kPairThreads) k_pairdep(PairArgs<DT> a) {
-    __shared__ int32_t s_t[32];
-    __shared__ int64_t s_dold[32], s_dnew[32];
-    __shared__ ff s_rold[32], s_rnew[32];
-    __shared__ const DT* s_pDo[32];
-    __shared__ const uint64_t* s_pSo[32];
-    __shared__ int s_u;
-    if (*a.err) return;
-    const int n = a.n;
-    const int64_t INF = Inf<DT>::v;
-    const int cnt = *a.count;
-    const int lane = threadIdx.x & 31;
-    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-        const int s = a.rows[i];
-        const int T = a.tcnt[s];
-        if (T == 0 || T > a.tcap) continue;   // block-uniform
-        const size_t rs = (size_t)s * n;
-        const bool snap_s = a.snapped[s] != 0;
-        const DT* Do_s = (snap_s ? a.sD : a.D) + rs;
-        const uint64_t* So_s = (snap_s ? a.sS : a.S) + rs;
-        const DT* Dn_s = a.D + rs;
-        const uint64_t* Sn_s = a.S + rs;
-        if (threadIdx.x < 32) {
-            const int val = lane < T ? a.tlist[(size_t)s * a.tcap + lane] : INT32_MAX;
-            bool dup = false;
-            for (int j = 0; j < 32; ++j) {
-                const int vj = __shfl_sync(0xffffffffu, val, j);
-                dup |= (vj == val) && (j < lane);
+__device__ __forceinline__ unsigned on_path(const DVec<DT, VN>& ds, const DVec<DT, VN>& dt, int64_t dst) {
+    using U = typename Unsigned<DT>::T;
+    unsigned m = 0;
+#pragma unroll
+    for (int q = 0; q < VN; ++q)
+        m |= (((U)ds.v[q] + (U)dt.v[q] == (U)dst) && dt.v[q] != 0) ? (1u << q) : 0u;
+    return m;
+}
+
+// Per-target scalars of the row being processed, as staged in shared memory.
+template <typename DT>
+struct TgtRows {
+    const DT* Do;           // row t before the update (saved copy or the state)
+    const DT* Dn;           // row t after it
+    int64_t dold, dnew;
+    const uint64_t* So;
+    const uint64_t* Sn;
+    ff rold, rnew;
+};
+
+// Weight of one work item of a listed row: its distinct targets plus one (the row's
+// own loads), or 0 when the row takes the full path or has nothing to correct.
+__device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0 || T > tcap) ? 0 : T + 1; }
+
+// wpre[i] = total weight of the items of listed rows 0..i-1 (nchunks items per row);
+// one CTA, a block scan per tile of rows.
+__global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
+                                                       const int32_t* tcnt, int tcap, int nchunks,
+                                                       int64_t* wpre, const int32_t* err) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t s_total;
+    if (*err) return;
+    const int cnt = *count;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    int64_t base = 0;
+    for (int tile = 0; tile < cnt; tile += blockDim.x) {
+        const int i = tile + tid;
+        const int64_t w = i < cnt ? item_weight(tcnt[rows[i]], tcap) * nchunks : 0;
+        int64_t incl = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int64_t x = lane < nw ? wsum[lane] : 0;
+            int64_t winc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, winc, o);
+                if (lane >= o) winc += y;
             }
-            const bool keep = !dup && val != INT32_MAX;
-            const unsigned km = __ballot_sync(0xffffffffu, keep);
-            int pos = 0;
-            for (int j = 0; j < 32; ++j) {
-                const int vj = __shfl_sync(0xffffffffu, val, j);
-                pos += ((km >> j) & 1u) && vj < val;
-            }
-            if (keep) {
-                const int t = val;
-                const size_t rt = (size_t)t * n;
-                const bool snap_t = a.snapped[t] != 0;
-                s_t[pos] = t;
-                s_pDo[pos] = (snap_t ? a.sD : a.D) + rt;
-                s_pSo[pos] = (snap_t ? a.sS : a.S) + rt;
-                const int64_t dol = Do_s[t], dnw = Dn_s[t];
-                const uint64_t sol = So_s[t], snw = Sn_s[t];
-                // -1: no shortest path (no column passes d(s,x) < -1)
-                s_dold[pos] = (dol == INF || sol == 0) ? -1 : dol;
-                s_dnew[pos] = (dnw == INF || snw == 0) ? -1 : dnw;
-                s_rold[pos] = sol ? ff_rcp(ff_from_u64(sol)) : ff{0.f, 0.f};
-                s_rnew[pos] = snw ? ff_rcp(ff_from_u64(snw)) : ff{0.f, 0.f};
-            }
-            if (lane == 0) s_u = __popc(km);
+            if (lane < nw) wsum[lane] = winc - x;
+            if (lane == 31) s_total = winc;
         }
         __syncthreads();
-        const int U = s_u;
-        for (int x0 = threadIdx.x * VN; x0 < n; x0 += blockDim.x * VN) {
-            int64_t dso[VN], dsn[VN];
-            load_d<DT, VN>(Do_s + x0, dso);
-            load_d<DT, VN>(Dn_s + x0, dsn);
-            ff acc[VN];
-            uint64_t sso[VN], ssn[VN];
-#pragma unroll
-            for (int q = 0; q < VN; ++q) acc[q] = ff{0.f, 0.f};
-            unsigned have_o = 0, have_n = 0, any = 0;
-            for (int u = 0; u < U; ++u) {
-                const int t = s_t[u];
-                const size_t rt = (size_t)t * n;
-                pair_terms<DT, VN>(x0, s, t, s_dold[u], s_rold[u], -1.f, dso, s_pDo[u], s_pSo[u], So_s, sso,
-                                   have_o, acc, any);
-                pair_terms<DT, VN>(x0, s, t, s_dnew[u], s_rnew[u], 1.f, dsn, a.D + rt, a.S + rt, Sn_s, ssn,
-                                   have_n, acc, any);
+        if (i < cnt) wpre[i] = base + wsum[wid] + incl - w;
+        base += s_total;
+        __syncthreads();
+    }
+    if (tid == 0) wpre[cnt] = base;
+}
+
+// Work item = (listed row s, chunk of CW = threads x VN columns).  Each CTA owns an
+// equal share of the total item weight (wpre) and runs, in order, the items whose
+// start falls in it, so rows with many targets spread over several CTAs and there is
+// no tail of one heavy CTA.  The plan of a row is staged in shared memory when the CTA
+// meets the row.  Per target a thread loads the old and the new row t at its VN
+// columns and finds the columns on a shortest s-t path with one add and compare each
+// (the rare matches read path counts).  sum_t [delta'_st(x) - delta_st(x)] is added to
+// delta_s(x) in the plan's target order (old term first), so the result does not
+// depend on how items are shared out.
+template <typename DT, int VN>
+__global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
+    __shared__ TgtRows<DT> s_tg[kPairCap];
+    __shared__ int s_i, s_c, s_snap;
+    if (*a.err) return;
+    constexpr int CW = kPairThreads * VN;
+    const int n = a.n;
+    const int nchunks = (n + CW - 1) / CW;
+    const int cnt = *a.count;
+    const int64_t W = a.wpre[cnt];
+    const int64_t lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
+    if (lo >= hi) return;   // block-uniform
+    if (threadIdx.x == 0) {
+        // last row whose items start at or before lo: wpre[L] <= lo < wpre[R]
+        int L = 0, R = cnt;
+        while (R - L > 1) {
+            const int m = (L + R) >> 1;
+            if (a.wpre[m] <= lo) L = m; else R = m;
+        }
+        const int64_t wc = (a.wpre[L + 1] - a.wpre[L]) / nchunks;   // > 0: lo lies in row L
+        s_i = L;
+        s_c = (int)((lo - a.wpre[L] + wc - 1) / wc);
+    }
+    __syncthreads();
+    int i = s_i, c = s_c;
+    int64_t wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
+    int cur = -1, s = -1, U = 0;
+    bool snap_s = false;
+    for (;;) {
+        if (c >= nchunks) {   // next row with items (block-uniform)
+            do {
+                ++i;
+            } while (i < cnt && a.wpre[i + 1] == a.wpre[i]);
+            if (i >= cnt) break;
+            wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
+            c = 0;
+        }
+        if (a.wpre[i] + (int64_t)c * wc >= hi) break;
+        if (i != cur) {
+            cur = i;
+            s = a.rows[i];
+            U = (int)wc - 1;
+            __syncthreads();   // the previous row's plan is no longer read
+            if (threadIdx.x == 0) s_snap = a.snapped[s];
+            if (threadIdx.x < U) {
+                const PairTgt p = a.plan[(size_t)s * a.tcap + threadIdx.x];
+                const size_t rt = (size_t)p.t * n;
+                TgtRows<DT> r;
+                r.Do = (p.snap_t ? a.sD : a.D) + rt;
+                r.Dn = a.D + rt;
+                r.So = (p.snap_t ? a.sS : a.S) + rt;
+                r.Sn = a.S + rt;
+                r.dold = p.dold;
+                r.dnew = p.dnew;
+                r.rold = p.rold;
+                r.rnew = p.rnew;
+                s_tg[threadIdx.x] = r;
             }
+            __syncthreads();
+            snap_s = s_snap != 0;
+        }
+        const int x0 = c * CW + threadIdx.x * VN;
+        ++c;
+        if (x0 >= n) continue;
+        const size_t rs = (size_t)s * n;
+        const uint64_t* So_s = (snap_s ? a.sS : a.S) + rs;
+        const uint64_t* Sn_s = a.S + rs;
+        DVec<DT, VN> dso, dsn;
+        dso.load((snap_s ? a.sD : a.D) + rs + x0);
+        dsn.load(a.D + rs + x0);
+        if (s >= x0 && s < x0 + VN) {
 #pragma unroll
             for (int q = 0; q < VN; ++q)
-                if ((any >> q) & 1u) a.Dl[rs + x0 + q] = ff_add(a.Dl[rs + x0 + q], acc[q]);
+                if (x0 + q == s) dso.v[q] = dsn.v[q] = (DT)Inf<DT>::v;
         }
-        __syncthreads();
+        ff acc[VN];
+#pragma unroll
+        for (int q = 0; q < VN; ++q) acc[q] = ff{0.f, 0.f};
+        unsigned any = 0;
+        for (int u = 0; u < U; ++u) {
+            const TgtRows<DT>& tg = s_tg[u];
+            const int64_t dold = tg.dold, dnew = tg.dnew;
+            DVec<DT, VN> dto, dtn;
+            bool ho = false, hn = false;
+            if (dold >= 0) dto.load(tg.Do + x0);
+            if (dnew >= 0) dtn.load(tg.Dn + x0);
+            if (dold >= 0) ho = any_sum<DT, VN>(dso, dto, dold);
+            if (dnew >= 0) hn = any_sum<DT, VN>(dsn, dtn, dnew);
+            if (!(ho | hn)) continue;
+            const unsigned mo = ho ? on_path<DT, VN>(dso, dto, dold) : 0u;
+            const unsigned mn = hn ? on_path<DT, VN>(dsn, dtn, dnew) : 0u;
+#pragma unroll
+            for (int q = 0; q < VN; ++q) {
+                const int x = x0 + q;
+                if ((mo >> q) & 1u) {
+                    const ff t = pair_term(So_s[x], tg.So[x], tg.rold);
+                    acc[q] = ff_add(acc[q], ff{-t.hi, -t.lo});
+                }
+                if ((mn >> q) & 1u) acc[q] = ff_add(acc[q], pair_term(Sn_s[x], tg.Sn[x], tg.rnew));
+            }
+            any |= mo | mn;
+        }
+#pragma unroll
+        for (int q = 0; q < VN; ++q)
+            if ((any >> q) & 1u) {
+                ff* p = a.Dl + rs + x0 + q;
+                *p = ff_add(*p, acc[q]);
+            }
     }
 }
 
@@ -244,11 +405,11 @@ void launch_snapshot(const Dev& d, const int32_t* rows, const int32_t* count, in
     if (d.dbytes == 4)
         k_snapshot<int32_t><<<grid, kSnapThreads, 0, d.st>>>(
             d.n, (const int32_t*)d.D, d.S, (int32_t*)d.snapD, d.snapS, d.snapped, rows, count, extra_row,
-            d.changed, d.tcnt, d.tcap, d.err);
+            d.changed, d.err);
     else
         k_snapshot<int64_t><<<grid, kSnapThreads, 0, d.st>>>(
             d.n, (const int64_t*)d.D, d.S, (int64_t*)d.snapD, d.snapS, d.snapped, rows, count, extra_row,
-            d.changed, d.tcnt, d.tcap, d.err);
+            d.changed, d.err);
 }
 
 void launch_full_flags(const Dev& d) {
@@ -271,6 +432,8 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.snapped = d.snapped;
     a.tcnt = d.tcnt;
     a.tlist = d.tlist;
+    a.plan = reinterpret_cast<PairTgt*>(d.plan);
+    a.wpre = d.pair_w;
     a.tcap = d.tcap;
     a.rows = d.acc_rows;
     a.count = d.counts + 1;
@@ -280,12 +443,19 @@ static PairArgs<DT> pair_args(const Dev& d) {
 }
 
 void launch_pairdep(const Dev& d) {
-    const int grid = d.nsm * 8;
+    const int pgrid = d.nsm * 8;
+    if (d.dbytes == 4) k_pair_plan<int32_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int32_t>(d));
+    else k_pair_plan<int64_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int64_t>(d));
+    const int vn = (d.dbytes == 4) ? (d.n % 4 == 0 ? 4 : 1) : (d.n % 2 == 0 ? 2 : 1);
+    const int cw = kPairThreads * vn;
+    k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
+                                          d.pair_w, d.err);
+    const int grid = d.nsm * 4;
     if (d.dbytes == 4) {
-        if (d.n % 4 == 0) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
+        if (vn == 4) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
         else k_pairdep<int32_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
     } else {
-        if (d.n % 2 == 0) k_pairdep<int64_t, 2><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
+        if (vn == 2) k_pairdep<int64_t, 2><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
         else k_pairdep<int64_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
     }
 }

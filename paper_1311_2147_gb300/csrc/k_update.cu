@@ -124,12 +124,19 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
     scan_stats(a.stats, n_changed, n_ties);
 }
 
+// Row v <- the OUT phase's result; with tcnt set, the columns whose distance or path
+// count changes are recorded as changed targets of row v.
 template <typename DT>
 __global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, const uint64_t* cS,
-                            const int32_t* err) {
+                            int32_t* tcnt, int32_t* tlist, int tcap, const int32_t* err) {
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) dev_write_row<DT>(t, n, D, S, v, cD, cS, err);
+    if (t >= n) return;
+    if (tcnt) {
+        const size_t i = (size_t)v * n + t;
+        if (D[i] != cD[t] || S[i] != cS[t]) record_target(tcnt, tlist, tcap, v, t);
+    }
+    dev_write_row<DT>(t, n, D, S, v, cD, cS, err);
 }
 
 // keep[e] = 1 when slot e holds an arc (a,b) with w(a,b) == d(a,b), i.e. an arc of E*
@@ -269,10 +276,14 @@ void launch_scan_out(const Dev& d, int32_t v) {
 void launch_write_row(const Dev& d, int32_t v) {
     if (d.dbytes == 4)
         k_write_row<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int32_t*)d.D, d.S, v,
-                                                                (const int32_t*)d.cD, d.cS, d.err);
+                                                                (const int32_t*)d.cD, d.cS,
+                                                                d.pair_on ? d.tcnt : nullptr, d.tlist,
+                                                                d.tcap, d.err);
     else
         k_write_row<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int64_t*)d.D, d.S, v,
-                                                                (const int64_t*)d.cD, d.cS, d.err);
+                                                                (const int64_t*)d.cD, d.cS,
+                                                                d.pair_on ? d.tcnt : nullptr, d.tlist,
+                                                                d.tcap, d.err);
 }
 
 void launch_estar_keep(const Dev& d, uint8_t* keep) {
