@@ -221,11 +221,11 @@ int bc_get_info(bc_graph* g, bc_info* out);
  * each launch on the handle's stream).  Classes: 0 the rank-1 pass (Lemma 2 / 4),
  * 1 dependency accumulation (Eq. 4 / Algorithm 1), 2 BC row sums, 3 per-vertex passes
  * (Algorithm 4 in both directions, row tests, row write), 4 bookkeeping (compaction,
- * E* writes, flags), 5 saving rows before their first write, 6 pair corrections of the
- * dependency rows ("pair_updates").  ms and launches are host arrays of BC_PROFILE_CLASSES entries (either
+ * E* writes, flags), 5 pair corrections of the dependency rows ("pair_updates").  ms
+ * and launches are host arrays of BC_PROFILE_CLASSES entries (either
  * may be NULL).  reset != 0 clears the sums after reading.  Synchronous.
  */
-enum { BC_PROFILE_CLASSES = 7 };
+enum { BC_PROFILE_CLASSES = 6 };
 int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
 
 /*
@@ -328,8 +328,9 @@ int bc_get_edges(bc_graph* g, int64_t* m, int32_t* src, int32_t* dst, int64_t* w
  * order; whenever a graph has nothing on the device, all its queued requests are
  * launched together on its own stream (continuous batching), so requests that arrive
  * while it is busy join its next launch and different graphs' launches overlap.  A
- * graph's device state (about n^2 * (distance bytes + 16) bytes, twice the distance
- * bytes + 24 for undirected graphs, which keep rows saved for pair corrections) is built only when
+ * graph's device state (about n^2 * (distance bytes + 16) bytes; twice the distance
+ * bytes + 24.125 for undirected graphs, which keep the old values of changed pairs for
+ * pair corrections) is built only when
  * the budget and the device's free memory leave room; when a graph with queued
  * requests needs room, idle graphs are evicted least-recently-used first and rebuilt
  * from their current edges when needed again.  Results are the same as applying each

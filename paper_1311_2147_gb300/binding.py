@@ -44,8 +44,7 @@ EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "
            "bc_batch_last_ms", "bc_batch_last_error", "bc_batch_destroy", "bc_get_edges",
            "bc_server_create", "bc_server_add_graph", "bc_server_submit", "bc_server_poll",
            "bc_server_pending", "bc_server_graph", "bc_server_stats", "bc_server_destroy"]
-PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping", "snapshot",
-                   "pair_corrections"]
+PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping", "pair_corrections"]
 
 
 class bc_info(ctypes.Structure):

@@ -446,7 +446,6 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
     if (kin) {
         timed(g, 3, 1, [&] { launch_alg4_in(d, v, d_ent, k); });
         timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
-        if (pair) timed(g, 5, 1, [&] { launch_snapshot(d, d.rows, d.counts, -1); });
         timed(g, 0, 1, [&] { launch_scan_in(d, v); });
     }
     if (kout) {
@@ -455,7 +454,6 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             launch_rows_out(d, v, d_ent, k);
         });
         timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
-        if (pair) timed(g, 5, 1, [&] { launch_snapshot(d, d.rows, d.counts, v); });
         timed(g, 0, 1, [&] { launch_scan_out(d, v); });
         timed(g, 3, 1, [&] { launch_write_row(d, v); });
     }
@@ -482,7 +480,7 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             CK(g, cudaStreamWaitEvent(d.st, g->ev_join, 0));
             g->launches += 4;
         } else {
-            timed(g, 6, 3, [&] { launch_pairdep(d); });
+            timed(g, 5, 3, [&] { launch_pairdep(d); });
             timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
         }
         timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
@@ -628,19 +626,21 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         destroy_all(g);
         return fail(nullptr, rc, "device allocation failed");
     }
-    // pair corrections (undirected graphs): saved rows, target lists, per-row flags
+    // pair corrections (undirected graphs): change map, old values of changed pairs,
+    // target lists and plans
     d.tcap = kPairCap;
+    d.chg_words = (n + 31) / 32;
     if (!dir) {
-        uint8_t* psD = nullptr;
-        if ((rc = dalloc(g, &psD, nn * (size_t)g->dbytes)) || (rc = dalloc(g, &d.snapS, nn)) ||
-            (rc = dalloc(g, &d.snapped, n)) || (rc = dalloc(g, &d.tcnt, n)) ||
+        uint8_t* poD = nullptr;
+        if ((rc = dalloc(g, &poD, nn * (size_t)g->dbytes)) || (rc = dalloc(g, &d.oldS, nn)) ||
+            (rc = dalloc(g, &d.chg, (size_t)n * d.chg_words)) || (rc = dalloc(g, &d.tcnt, n)) ||
             (rc = dalloc(g, &d.tlist, (size_t)n * kPairCap)) || (rc = dalloc(g, &d.full_rows, n)) ||
             (rc = dalloc(g, reinterpret_cast<uint8_t**>(&d.plan), (size_t)n * kPairCap * 40)) ||
             (rc = dalloc(g, &d.pair_w, (size_t)n + 1))) {
             destroy_all(g);
             return fail(nullptr, rc, "device allocation failed");
         }
-        d.snapD = psD;
+        d.oldD = poD;
         d.pair_on = 1;
     }
     if (cudaMallocHost(&g->h_err, sizeof(int32_t)) != cudaSuccess ||
@@ -674,7 +674,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     CKI(cudaMemsetAsync(d.changed, 0, n, d.st));
     CKI(cudaMemsetAsync(d.counts, 0, 8 * sizeof(int32_t), d.st));
     if (!dir) {
-        CKI(cudaMemsetAsync(d.snapped, 0, n, d.st));
+        CKI(cudaMemsetAsync(d.chg, 0, sizeof(uint32_t) * n * d.chg_words, d.st));
         CKI(cudaMemsetAsync(d.tcnt, 0, sizeof(int32_t) * n, d.st));
     }
     CKI(cudaStreamSynchronize(d.st));

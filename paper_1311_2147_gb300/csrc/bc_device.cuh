@@ -218,16 +218,8 @@ struct ScanArgs {
     int skip_row;
     int32_t* err;
     int64_t* stats;        // [4] pairs with a lower distance [5] pairs with new tied paths [6] rows
-    int32_t* tcnt;         // when set: record every changed pair (s, t) as target t of row s
-    int32_t* tlist;
-    int32_t tcap;
+    PairRec rec;           // when rec.tcnt is set: record the changed pairs (pair corrections)
 };
-
-// Record t as a changed target of row s (entries beyond the capacity are only counted).
-__device__ __forceinline__ void record_target(int32_t* tcnt, int32_t* tlist, int tcap, int s, int t) {
-    const int pos = atomicAdd(tcnt + s, 1);
-    if (pos < tcap) tlist[(size_t)s * tcap + pos] = t;
-}
 
 // The rank-1 rule of Lemma 2 / Lemma 4 for one pair, given the candidate distance
 // cand = rd + cd through v:  cand > d: unchanged;  cand == d: sigma += rowM * colM
@@ -316,14 +308,15 @@ __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int6
                 const int64_t cand = dsum<DT>(rd, cd[q]);
                 int64_t nd;
                 const int ties0 = n_ties;
+                const uint64_t sig0 = a.rec.tcnt ? a.S[rowoff + t + q] : 0ull;
                 if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q],
                                   a.S, a.err, &nd, &n_ties)) {
                     V::set(dv[u], q, nd);
                     wr = true;
                     ++n_changed;
-                    if (a.tcnt) record_target(a.tcnt, a.tlist, a.tcap, s, t + q);
-                } else if (n_ties != ties0 && a.tcnt) {
-                    record_target(a.tcnt, a.tlist, a.tcap, s, t + q);
+                    if (a.rec.tcnt) record_change<DT>(a.rec, n, s, t + q, dd[q], sig0);
+                } else if (n_ties != ties0 && a.rec.tcnt) {
+                    record_change<DT>(a.rec, n, s, t + q, dd[q], sig0);
                 }
             }
             if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv[u];
@@ -336,12 +329,13 @@ __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int6
             const int64_t cand = dsum<DT>(rd, cd);
             int64_t nd;
             const int ties0 = n_ties;
+            const uint64_t sig0 = a.rec.tcnt ? a.S[rowoff + t] : 0ull;
             if (pair_rule<DT>(cand, old, rowoff + t, rs, rm, a.cS[t], a.cM[t], a.S, a.err, &nd, &n_ties)) {
                 Drow[t] = (DT)nd;
                 ++n_changed;
-                if (a.tcnt) record_target(a.tcnt, a.tlist, a.tcap, s, t);
-            } else if (n_ties != ties0 && a.tcnt) {
-                record_target(a.tcnt, a.tlist, a.tcap, s, t);
+                if (a.rec.tcnt) record_change<DT>(a.rec, n, s, t, old, sig0);
+            } else if (n_ties != ties0 && a.rec.tcnt) {
+                record_change<DT>(a.rec, n, s, t, old, sig0);
             }
         }
     }

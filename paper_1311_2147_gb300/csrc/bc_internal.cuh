@@ -158,14 +158,15 @@ struct Dev {
     int32_t acc_mask_smem;  // 1: the DAG slot mask lives in shared memory
     int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
     int64_t ws_stride;
-    // pair-dependency corrections (undirected graphs): rows as they were before the
-    // update, and the targets whose pair changed in each row
+    // pair-dependency corrections (undirected graphs): the pairs changed by this update,
+    // their values before it, and the changed targets of each row
     int32_t pair_on;
     int32_t tcap;        // targets recorded per row (kPairCap); more -> full re-accumulation
-    void* snapD;         // [n*n] distance rows saved before their first change (DT)
-    uint64_t* snapS;     // [n*n] path-count rows saved likewise
-    uint8_t* snapped;    // [n] row saved in this update
-    int32_t* tcnt;       // [n] changed targets recorded for the row
+    uint32_t* chg;       // [n * chg_words] bit (s,t): pair changed in this update
+    int32_t chg_words;   // (n + 31) / 32
+    void* oldD;          // [n*n] d(s,t) before the update, valid where the bit is set (DT)
+    uint64_t* oldS;      // [n*n] sigma_st before the update, likewise
+    int32_t* tcnt;       // [n] changed targets of the row
     int32_t* tlist;      // [n * tcap]
     void* plan;          // [n * tcap] per-target scalars of the pair corrections (k_pair.cu)
     int64_t* pair_w;     // [n + 1] prefix of the pair corrections' work item weights
@@ -180,6 +181,34 @@ constexpr int kAccThreads = 512;
 // acc_mask_smem and ws_stride of d); the work space must then hold acc_grid * ws_stride.
 void accum_config(Dev& d);
 
+// Recording of changed pairs by the passes that write D and sigma (pair corrections).
+struct PairRec {
+    uint32_t* chg;
+    int32_t chg_words;
+    void* oldD;
+    uint64_t* oldS;
+    int32_t* tcnt;       // NULL: nothing is recorded
+    int32_t* tlist;
+    int32_t tcap;
+};
+
+// The first change of pair (s,t) in an update sets its bit, saves its old distance and
+// path count, and lists t as a changed target of row s (targets beyond the capacity
+// are only counted).  Later changes of the same pair (the OUT phase after the IN
+// phase) keep the saved values.
+template <typename DT>
+__device__ __forceinline__ void record_change(const PairRec& r, int n, int s, int t, int64_t d_old,
+                                              uint64_t sig_old) {
+    const uint32_t bit = 1u << (t & 31);
+    const uint32_t prev = atomicOr(r.chg + (size_t)s * r.chg_words + (t >> 5), bit);
+    if (prev & bit) return;
+    const size_t i = (size_t)s * n + t;
+    static_cast<DT*>(r.oldD)[i] = (DT)d_old;
+    r.oldS[i] = sig_old;
+    const int pos = atomicAdd(r.tcnt + s, 1);
+    if (pos < r.tcap) r.tlist[(size_t)s * r.tcap + pos] = t;
+}
+
 // ---- launches (k_update.cu) ----
 void launch_estar_write(const Dev& d, const EOps& ops);
 void launch_estar_move(const Dev& d, const EMoves& moves);
@@ -192,7 +221,7 @@ void launch_scan_in(const Dev& d, int32_t v);
 void launch_scan_out(const Dev& d, int32_t v);
 void launch_write_row(const Dev& d, int32_t v);
 void launch_estar_keep(const Dev& d, uint8_t* keep);
-void launch_snapshot(const Dev& d, const int32_t* rows, const int32_t* count, int32_t extra_row);
+PairRec pair_rec(const Dev& d);
 void launch_full_flags(const Dev& d);
 void launch_pairdep(const Dev& d);
 void launch_pair_clear(const Dev& d);

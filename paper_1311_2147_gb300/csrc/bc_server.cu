@@ -69,9 +69,11 @@ namespace {
 
 int64_t state_bytes(int32_t n, uint32_t flags) {
     const int64_t sd = (flags & BC_DIST_I64) ? 8 : 4;
-    // D, sigma, delta; undirected graphs also keep the rows saved for pair corrections
-    const int64_t per_pair = (sd + 16) + ((flags & BC_UNDIRECTED) ? sd + 8 : 0);
-    return (int64_t)n * n * per_pair + (int64_t)n * 256 + (64 << 20);
+    // D, sigma, delta; undirected graphs also keep the old values of changed pairs and
+    // the change map (one bit per pair) for pair corrections
+    const bool und = (flags & BC_UNDIRECTED) != 0;
+    const int64_t per_pair = (sd + 16) + (und ? sd + 8 : 0);
+    return (int64_t)n * n * per_pair + (und ? (int64_t)n * n / 8 : 0) + (int64_t)n * 256 + (64 << 20);
 }
 
 int evict(bc_server* s, int32_t gid) {

@@ -9,15 +9,15 @@
 // shortest, and since sigma_st did not grow no path joined them.  Every delta_st(x) of
 // such a pair is unchanged, hence
 //     delta'_s(x) = delta_s(x) + sum over changed pairs (s,t) of [delta'_st(x) - delta_st(x)].
-// The rank-1 passes record the changed targets t of every row s (Lemma 2 / Lemma 4:
-// a lower distance, or new tied paths).  A row with at most kPairCap of them is
-// corrected by this sum; the old terms read the rows as they were before the update,
-// which k_snapshot saves before the first write to each row, and the new terms read
-// the state after both phases.  In G_D of an undirected graph d(x,t) = d(t,x) and
-// sigma_xt = sigma_tx before and after the update, so the column t of the formula is
-// row t, read contiguously.  Row v, which the OUT phase rewrites whole, records the
-// targets where its new values differ.  Rows with more targets than the cap are
-// re-accumulated by Algorithm 1 instead.
+// The passes that write D and sigma (the rank-1 passes of Lemma 2 / Lemma 4 and the
+// write of row v) record each pair's first change in an update: a bit in the n x n
+// change map, the pair's old distance and path count, and t in the target list of row
+// s (record_change).  A row with at most kPairCap changed targets is corrected by the
+// sum above.  The state before the update is the state after it except at the set
+// bits, where the saved values hold, so both terms read the current rows plus a few
+// saved values.  In G_D of an undirected graph d(x,t) = d(t,x) and sigma_xt = sigma_tx
+// before and after the update, so the column t of the formula is row t, read
+// contiguously.  Rows with more targets than the cap are re-accumulated by Algorithm 1.
 #include "bc_device.cuh"
 #include "ff.cuh"
 
@@ -25,49 +25,8 @@ static_assert(bcg::kPairCap <= 1024, "the targets of a row are sorted by one CTA
 
 namespace bcg {
 
-constexpr int kSnapThreads = 256;
 constexpr int kPairThreads = 256;
-
-// Save rows[0..count) (and row extra_row when the OUT phase changes it) before their
-// first write in this update.  The rows of one launch are distinct.
-template <typename DT>
-__global__ void __launch_bounds__(kSnapThreads)
-k_snapshot(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S, DT* sD, uint64_t* sS,
-           uint8_t* snapped, const int32_t* rows, const int32_t* count, int extra_row,
-           const uint8_t* changed, const int32_t* err) {
-    __shared__ int s_do;
-    if (*err) return;
-    const int cnt = *count;
-    const int items = cnt + (extra_row >= 0 ? 1 : 0);
-    for (int i = blockIdx.x; i < items; i += gridDim.x) {
-        const int s = i < cnt ? rows[i] : extra_row;
-        if (threadIdx.x == 0) {
-            int go = snapped[s] == 0;
-            if (i >= cnt) go = go && changed[s] != 0;
-            if (go) snapped[s] = 1;
-            s_do = go;
-        }
-        __syncthreads();
-        const bool go = s_do != 0;
-        __syncthreads();
-        if (!go) continue;
-        const size_t off = (size_t)s * n;
-        if ((n & 3) == 0 && sizeof(DT) == 4) {
-            const int4* a = reinterpret_cast<const int4*>(D + off);
-            int4* b = reinterpret_cast<int4*>(sD + off);
-            for (int j = threadIdx.x; j < n / 4; j += blockDim.x) b[j] = __ldcs(a + j);
-        } else {
-            for (int j = threadIdx.x; j < n; j += blockDim.x) sD[off + j] = D[off + j];
-        }
-        if ((n & 1) == 0) {
-            const ulonglong2* a = reinterpret_cast<const ulonglong2*>(S + off);
-            ulonglong2* b = reinterpret_cast<ulonglong2*>(sS + off);
-            for (int j = threadIdx.x; j < n / 2; j += blockDim.x) b[j] = __ldcs(a + j);
-        } else {
-            for (int j = threadIdx.x; j < n; j += blockDim.x) sS[off + j] = S[off + j];
-        }
-    }
-}
+constexpr int kPairCtasPerSm = 4;
 
 // mark[s] = row s changed and has more recorded targets than the cap.
 __global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt, int tcap, uint8_t* mark) {
@@ -75,31 +34,33 @@ __global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt,
     if (s < n) mark[s] = (changed[s] != 0 && tcnt[s] > tcap) ? 1 : 0;
 }
 
-// Per-update flags of the rows listed in rows[0..count) back to zero; the rows sent to
-// the full path are added to stats[7].
-__global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t* tcnt, uint8_t* snapped,
+// Per-update records of the rows listed in rows[0..count) back to zero (a pair (s,t)
+// changes only in a changed row s); the rows sent to the full path are added to
+// stats[7].
+__global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t* tcnt, uint32_t* chg, int words,
                              const int32_t* full_count, int64_t* stats) {
     const int cnt = *count;
     if (blockIdx.x == 0 && threadIdx.x == 0) stats[7] += *full_count;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int64_t total = (int64_t)cnt * words;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(j / words), w = (int)(j - (int64_t)i * words);
         const int s = rows[i];
-        tcnt[s] = 0;
-        snapped[s] = 0;
+        chg[(size_t)s * words + w] = 0u;
+        if (w == 0) tcnt[s] = 0;
     }
 }
 
 // One changed target t of a row s, as prepared by k_pair_plan: the pair's distance and
-// reciprocal path count before and after the update (-1: no path), and whether row t
-// was saved (its old values then come from the saved copy).
+// reciprocal path count before and after the update (-1: no path).
 struct PairTgt {
     int32_t t;
-    int32_t snap_t;
+    int32_t pad;
     int64_t dold;
     int64_t dnew;
     ff rold;
     ff rnew;
 };
-
 static_assert(sizeof(PairTgt) == 40, "the plan is allocated with 40 bytes per target");
 
 template <typename DT>
@@ -107,10 +68,11 @@ struct PairArgs {
     int n;
     const DT* D;            // state after the update
     const uint64_t* S;
-    const DT* sD;           // rows saved before the update (where snapped)
-    const uint64_t* sS;
-    const uint8_t* snapped;
-    int32_t* tcnt;          // recorded targets per row; k_pair_plan replaces it by the unique count
+    const uint32_t* chg;    // change map: bit (s,x) set where the pair changed
+    int words;
+    const DT* oD;           // old values where the bit is set
+    const uint64_t* oS;
+    int32_t* tcnt;          // changed targets per row
     const int32_t* tlist;
     PairTgt* plan;          // [n * tcap]
     int64_t* wpre;          // [n + 1] prefix of the item weights of the listed rows
@@ -121,15 +83,14 @@ struct PairArgs {
     int32_t* err;
 };
 
-// One CTA (kPlanThreads >= tcap threads) per listed row with 1..tcap recorded targets:
-// sort them, drop repeats (a pair can change in both phases), and write the per-target
-// scalars of the plan; tcnt[s] becomes the number of distinct targets.
+// One CTA (kPlanThreads >= tcap threads) per listed row with 1..tcap changed targets:
+// sort them (the sums then run in a fixed order) and write the per-target scalars of
+// the plan.  Every target of row s has its bit set, so its old values are the saved ones.
 constexpr int kPlanThreads = kPairCap;
 
 template <typename DT>
 __global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
     __shared__ int32_t s_val[kPlanThreads];
-    __shared__ int s_first[kPlanThreads];
     if (*a.err) return;
     const int n = a.n;
     const int64_t INF = Inf<DT>::v;
@@ -142,29 +103,21 @@ __global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
         const int val = tid < T ? a.tlist[(size_t)s * a.tcap + tid] : INT32_MAX;
         s_val[tid] = val;
         __syncthreads();
-        bool first = val != INT32_MAX;
-        for (int j = 0; j < tid && first; ++j) first = s_val[j] != val;
-        s_first[tid] = first;
-        __syncthreads();
         int pos = 0;
-        for (int j = 0; j < T; ++j) pos += s_first[j] && s_val[j] < val;
-        const int U = __syncthreads_count(first);
-        if (first) {
-            const size_t rs = (size_t)s * n;
-            const bool snap_s = a.snapped[s] != 0;
-            const int t = val;
-            const int64_t dol = (snap_s ? a.sD : a.D)[rs + t], dnw = a.D[rs + t];
-            const uint64_t sol = (snap_s ? a.sS : a.S)[rs + t], snw = a.S[rs + t];
+        for (int j = 0; j < T; ++j) pos += s_val[j] < val;   // targets are distinct
+        if (tid < T) {
+            const size_t it = (size_t)s * n + val;
+            const int64_t dol = a.oD[it], dnw = a.D[it];
+            const uint64_t sol = a.oS[it], snw = a.S[it];
             PairTgt p;
-            p.t = t;
-            p.snap_t = a.snapped[t] != 0;
+            p.t = val;
+            p.pad = 0;
             p.dold = (dol == INF || sol == 0) ? -1 : dol;
             p.dnew = (dnw == INF || snw == 0) ? -1 : dnw;
             p.rold = sol ? ff_rcp(ff_from_u64(sol)) : ff{0.f, 0.f};
             p.rnew = snw ? ff_rcp(ff_from_u64(snw)) : ff{0.f, 0.f};
             a.plan[(size_t)s * a.tcap + pos] = p;
         }
-        if (tid == 0) a.tcnt[s] = U;
         __syncthreads();
     }
 }
@@ -191,6 +144,24 @@ struct DVec {
         }
     }
 };
+
+// Bits of columns x0 .. x0+VN-1 of row r in the change map (x0 is a multiple of VN, so
+// they sit in one word).
+template <int VN>
+__device__ __forceinline__ unsigned chg_bits(const uint32_t* chg, int words, int r, int x0) {
+    return (chg[(size_t)r * words + (x0 >> 5)] >> (x0 & 31)) & ((1u << VN) - 1u);
+}
+
+// The old values of row r at the columns whose bit is set (one vector load; the saved
+// values at the other columns are stale and not used).
+template <typename DT, int VN>
+__device__ __forceinline__ void patch_old(DVec<DT, VN>& d, unsigned bits, const DT* oD_row, int x0) {
+    DVec<DT, VN> o;
+    o.load(oD_row + x0);
+#pragma unroll
+    for (int q = 0; q < VN; ++q)
+        if ((bits >> q) & 1u) d.v[q] = o.v[q];
+}
 
 template <typename DT> struct Unsigned;
 template <> struct Unsigned<int32_t> { using T = uint32_t; };
@@ -222,18 +193,15 @@ __device__ __forceinline__ unsigned on_path(const DVec<DT, VN>& ds, const DVec<D
 }
 
 // Per-target scalars of the row being processed, as staged in shared memory.
-template <typename DT>
-struct TgtRows {
-    const DT* Do;           // row t before the update (saved copy or the state)
-    const DT* Dn;           // row t after it
+struct TgtRow {
+    int32_t t;
+    int32_t pad;
     int64_t dold, dnew;
-    const uint64_t* So;
-    const uint64_t* Sn;
     ff rold, rnew;
 };
 
-// Weight of one work item of a listed row: its distinct targets plus one (the row's
-// own loads), or 0 when the row takes the full path or has nothing to correct.
+// Weight of one work item of a listed row: its targets plus one (the row's own loads),
+// or 0 when the row takes the full path or has nothing to correct.
 __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0 || T > tcap) ? 0 : T + 1; }
 
 // wpre[i] = total weight of the items of listed rows 0..i-1 (nchunks items per row);
@@ -282,15 +250,16 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
 // equal share of the total item weight (wpre) and runs, in order, the items whose
 // start falls in it, so rows with many targets spread over several CTAs and there is
 // no tail of one heavy CTA.  The plan of a row is staged in shared memory when the CTA
-// meets the row.  Per target a thread loads the old and the new row t at its VN
-// columns and finds the columns on a shortest s-t path with one add and compare each
-// (the rare matches read path counts).  sum_t [delta'_st(x) - delta_st(x)] is added to
-// delta_s(x) in the plan's target order (old term first), so the result does not
-// depend on how items are shared out.
+// meets the row.  Per target a thread loads row t at its VN columns once (the old
+// values differ only where the change map has a bit) and finds the columns on a
+// shortest s-t path with one add and compare per column and state (the rare matches
+// read path counts).  sum_t [delta'_st(x) - delta_st(x)] is added to delta_s(x) in the
+// plan's target order (old term first), so the result does not depend on how items
+// are shared out.
 template <typename DT, int VN>
-__global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
-    __shared__ TgtRows<DT> s_tg[kPairCap];
-    __shared__ int s_i, s_c, s_snap;
+__global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairArgs<DT> a) {
+    __shared__ TgtRow s_tg[kPairCap];
+    __shared__ int s_i, s_c;
     if (*a.err) return;
     constexpr int CW = kPairThreads * VN;
     const int n = a.n;
@@ -314,7 +283,6 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
     int i = s_i, c = s_c;
     int64_t wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
     int cur = -1, s = -1, U = 0;
-    bool snap_s = false;
     for (;;) {
         if (c >= nchunks) {   // next row with items (block-uniform)
             do {
@@ -330,33 +298,21 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
             s = a.rows[i];
             U = (int)wc - 1;
             __syncthreads();   // the previous row's plan is no longer read
-            if (threadIdx.x == 0) s_snap = a.snapped[s];
             if (threadIdx.x < U) {
                 const PairTgt p = a.plan[(size_t)s * a.tcap + threadIdx.x];
-                const size_t rt = (size_t)p.t * n;
-                TgtRows<DT> r;
-                r.Do = (p.snap_t ? a.sD : a.D) + rt;
-                r.Dn = a.D + rt;
-                r.So = (p.snap_t ? a.sS : a.S) + rt;
-                r.Sn = a.S + rt;
-                r.dold = p.dold;
-                r.dnew = p.dnew;
-                r.rold = p.rold;
-                r.rnew = p.rnew;
-                s_tg[threadIdx.x] = r;
+                s_tg[threadIdx.x] = TgtRow{p.t, 0, p.dold, p.dnew, p.rold, p.rnew};
             }
             __syncthreads();
-            snap_s = s_snap != 0;
         }
         const int x0 = c * CW + threadIdx.x * VN;
         ++c;
         if (x0 >= n) continue;
         const size_t rs = (size_t)s * n;
-        const uint64_t* So_s = (snap_s ? a.sS : a.S) + rs;
-        const uint64_t* Sn_s = a.S + rs;
-        DVec<DT, VN> dso, dsn;
-        dso.load((snap_s ? a.sD : a.D) + rs + x0);
+        DVec<DT, VN> dsn;
         dsn.load(a.D + rs + x0);
+        const unsigned bs = chg_bits<VN>(a.chg, a.words, s, x0);
+        DVec<DT, VN> dso = dsn;
+        if (bs) patch_old<DT, VN>(dso, bs, a.oD + rs, x0);
         if (s >= x0 && s < x0 + VN) {
 #pragma unroll
             for (int q = 0; q < VN; ++q)
@@ -367,14 +323,16 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
         for (int q = 0; q < VN; ++q) acc[q] = ff{0.f, 0.f};
         unsigned any = 0;
         for (int u = 0; u < U; ++u) {
-            const TgtRows<DT>& tg = s_tg[u];
+            const TgtRow& tg = s_tg[u];
             const int64_t dold = tg.dold, dnew = tg.dnew;
-            DVec<DT, VN> dto, dtn;
-            bool ho = false, hn = false;
-            if (dold >= 0) dto.load(tg.Do + x0);
-            if (dnew >= 0) dtn.load(tg.Dn + x0);
-            if (dold >= 0) ho = any_sum<DT, VN>(dso, dto, dold);
-            if (dnew >= 0) hn = any_sum<DT, VN>(dsn, dtn, dnew);
+            const size_t rt = (size_t)tg.t * n;
+            DVec<DT, VN> dtn;
+            dtn.load(a.D + rt + x0);
+            const unsigned bt = chg_bits<VN>(a.chg, a.words, tg.t, x0);
+            DVec<DT, VN> dto = dtn;
+            if (bt) patch_old<DT, VN>(dto, bt, a.oD + rt, x0);
+            const bool ho = dold >= 0 && any_sum<DT, VN>(dso, dto, dold);
+            const bool hn = dnew >= 0 && any_sum<DT, VN>(dsn, dtn, dnew);
             if (!(ho | hn)) continue;
             const unsigned mo = ho ? on_path<DT, VN>(dso, dto, dold) : 0u;
             const unsigned mn = hn ? on_path<DT, VN>(dsn, dtn, dnew) : 0u;
@@ -382,10 +340,12 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
             for (int q = 0; q < VN; ++q) {
                 const int x = x0 + q;
                 if ((mo >> q) & 1u) {
-                    const ff t = pair_term(So_s[x], tg.So[x], tg.rold);
+                    const uint64_t ssx = ((bs >> q) & 1u) ? a.oS[rs + x] : a.S[rs + x];
+                    const uint64_t stx = ((bt >> q) & 1u) ? a.oS[rt + x] : a.S[rt + x];
+                    const ff t = pair_term(ssx, stx, tg.rold);
                     acc[q] = ff_add(acc[q], ff{-t.hi, -t.lo});
                 }
-                if ((mn >> q) & 1u) acc[q] = ff_add(acc[q], pair_term(Sn_s[x], tg.Sn[x], tg.rnew));
+                if ((mn >> q) & 1u) acc[q] = ff_add(acc[q], pair_term(a.S[rs + x], a.S[rt + x], tg.rnew));
             }
             any |= mo | mn;
         }
@@ -400,16 +360,16 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pairdep(PairArgs<DT> a) {
 
 // ------------------------------------------------------------------ launches
 
-void launch_snapshot(const Dev& d, const int32_t* rows, const int32_t* count, int32_t extra_row) {
-    const int grid = d.nsm * 4;
-    if (d.dbytes == 4)
-        k_snapshot<int32_t><<<grid, kSnapThreads, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.S, (int32_t*)d.snapD, d.snapS, d.snapped, rows, count, extra_row,
-            d.changed, d.err);
-    else
-        k_snapshot<int64_t><<<grid, kSnapThreads, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.S, (int64_t*)d.snapD, d.snapS, d.snapped, rows, count, extra_row,
-            d.changed, d.err);
+PairRec pair_rec(const Dev& d) {
+    PairRec r;
+    r.chg = d.chg;
+    r.chg_words = d.chg_words;
+    r.oldD = d.oldD;
+    r.oldS = d.oldS;
+    r.tcnt = d.tcnt;
+    r.tlist = d.tlist;
+    r.tcap = d.tcap;
+    return r;
 }
 
 void launch_full_flags(const Dev& d) {
@@ -417,8 +377,8 @@ void launch_full_flags(const Dev& d) {
 }
 
 void launch_pair_clear(const Dev& d) {
-    k_pair_clear<<<std::max(1, std::min(d.nsm, (d.n + 255) / 256)), 256, 0, d.st>>>(
-        d.acc_rows, d.counts + 1, d.tcnt, d.snapped, d.counts + 3, d.stats);
+    k_pair_clear<<<d.nsm * 4, 256, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.chg, d.chg_words,
+                                              d.counts + 3, d.stats);
 }
 
 template <typename DT>
@@ -427,9 +387,10 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.n = d.n;
     a.D = (const DT*)d.D;
     a.S = d.S;
-    a.sD = (const DT*)d.snapD;
-    a.sS = d.snapS;
-    a.snapped = d.snapped;
+    a.chg = d.chg;
+    a.words = d.chg_words;
+    a.oD = (const DT*)d.oldD;
+    a.oS = d.oldS;
     a.tcnt = d.tcnt;
     a.tlist = d.tlist;
     a.plan = reinterpret_cast<PairTgt*>(d.plan);
@@ -450,7 +411,7 @@ void launch_pairdep(const Dev& d) {
     const int cw = kPairThreads * vn;
     k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
                                           d.pair_w, d.err);
-    const int grid = d.nsm * 4;
+    const int grid = d.nsm * kPairCtasPerSm;   // one wave: the split of the work is static
     if (d.dbytes == 4) {
         if (vn == 4) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
         else k_pairdep<int32_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));

@@ -124,17 +124,17 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
     scan_stats(a.stats, n_changed, n_ties);
 }
 
-// Row v <- the OUT phase's result; with tcnt set, the columns whose distance or path
-// count changes are recorded as changed targets of row v.
+// Row v <- the OUT phase's result; with rec.tcnt set, the pairs (v,t) whose distance or
+// path count changes are recorded.
 template <typename DT>
-__global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, const uint64_t* cS,
-                            int32_t* tcnt, int32_t* tlist, int tcap, const int32_t* err) {
+__global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, const uint64_t* cS, PairRec rec,
+                            const int32_t* err) {
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    if (tcnt) {
+    if (rec.tcnt) {
         const size_t i = (size_t)v * n + t;
-        if (D[i] != cD[t] || S[i] != cS[t]) record_target(tcnt, tlist, tcap, v, t);
+        if (D[i] != cD[t] || S[i] != cS[t]) record_change<DT>(rec, n, v, t, D[i], S[i]);
     }
     dev_write_row<DT>(t, n, D, S, v, cD, cS, err);
 }
@@ -230,9 +230,7 @@ static ScanArgs<DT> scan_args(const Dev& d) {
     a.skip_row = -1;
     a.err = d.err;
     a.stats = d.stats;
-    a.tcnt = d.pair_on ? d.tcnt : nullptr;
-    a.tlist = d.tlist;
-    a.tcap = d.tcap;
+    a.rec = d.pair_on ? pair_rec(d) : PairRec{};
     return a;
 }
 
@@ -277,13 +275,11 @@ void launch_write_row(const Dev& d, int32_t v) {
     if (d.dbytes == 4)
         k_write_row<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int32_t*)d.D, d.S, v,
                                                                 (const int32_t*)d.cD, d.cS,
-                                                                d.pair_on ? d.tcnt : nullptr, d.tlist,
-                                                                d.tcap, d.err);
+                                                                d.pair_on ? pair_rec(d) : PairRec{}, d.err);
     else
         k_write_row<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int64_t*)d.D, d.S, v,
                                                                 (const int64_t*)d.cD, d.cS,
-                                                                d.pair_on ? d.tcnt : nullptr, d.tlist,
-                                                                d.tcap, d.err);
+                                                                d.pair_on ? pair_rec(d) : PairRec{}, d.err);
 }
 
 void launch_estar_keep(const Dev& d, uint8_t* keep) {

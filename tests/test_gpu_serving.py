@@ -66,7 +66,7 @@ def test_serving_mix_equals_alone(budget_graphs):
         budget = 1 << 36
     else:
         nmax = max(g.n for g, _ in fam)
-        budget = budget_graphs * (nmax * nmax * 32 + nmax * 256 + (64 << 20))
+        budget = budget_graphs * (nmax * nmax * 33 + nmax * 256 + (64 << 20))
     srv = binding.BCServer(budget, max_batch=8)
     gids = [srv.add_graph(g) for g, _ in fam]
     results = []
