@@ -167,23 +167,14 @@ template <typename DT> struct Unsigned;
 template <> struct Unsigned<int32_t> { using T = uint32_t; };
 template <> struct Unsigned<int64_t> { using T = uint64_t; };
 
-// Whether some column x0+q can lie on a shortest s-t path of one state:
-// d(s,x) + d(x,t) = d(s,t).  Distances are below INF = DT max, so their unsigned sum
-// never wraps, and a sum with an INF term exceeds every finite d(s,t).  (The caller
-// replaces d(s,s) by INF; x = t, where d(x,t) = 0, is excluded by on_path.)
+// Bit q set where column x0+q lies on a shortest s-t path of one state:
+// d(s,x) + d(x,t) = d(s,t) and d(x,t) > 0 (x != t; x != s is ensured by the caller,
+// which replaces d(s,s) by INF).  Distances are below INF = DT max, so their unsigned
+// sum never wraps, and a sum with an INF term exceeds every finite d(s,t); "no path"
+// is passed as all ones, which no sum equals.
 template <typename DT, int VN>
-__device__ __forceinline__ bool any_sum(const DVec<DT, VN>& ds, const DVec<DT, VN>& dt, int64_t dst) {
-    using U = typename Unsigned<DT>::T;
-    bool hit = false;
-#pragma unroll
-    for (int q = 0; q < VN; ++q) hit |= (U)ds.v[q] + (U)dt.v[q] == (U)dst;
-    return hit;
-}
-
-// Bit q set where column x0+q lies on a shortest s-t path: the sum matches and
-// d(x,t) > 0.
-template <typename DT, int VN>
-__device__ __forceinline__ unsigned on_path(const DVec<DT, VN>& ds, const DVec<DT, VN>& dt, int64_t dst) {
+__device__ __forceinline__ unsigned on_path(const DVec<DT, VN>& ds, const DVec<DT, VN>& dt,
+                                            typename Unsigned<DT>::T dst) {
     using U = typename Unsigned<DT>::T;
     unsigned m = 0;
 #pragma unroll
@@ -192,13 +183,21 @@ __device__ __forceinline__ unsigned on_path(const DVec<DT, VN>& ds, const DVec<D
     return m;
 }
 
-// Per-target scalars of the row being processed, as staged in shared memory.
-struct TgtRow {
-    int32_t t;
-    int32_t pad;
-    int64_t dold, dnew;
+// Per-target scalars of the row being processed, as staged in shared memory: what
+// every column test reads (row t of D and of the change map, and the distances, with
+// -1 for "no path": in unsigned arithmetic no sum of two distances equals it) and
+// what only a matched column reads.
+template <typename DT>
+struct TgtFast {
+    const DT* Dt;
+    const uint32_t* Ct;
+    DT dold, dnew;
+};
+struct TgtSlow {
+    int64_t rt;      // t * n
     ff rold, rnew;
 };
+
 
 // Weight of one work item of a listed row: its targets plus one (the row's own loads),
 // or 0 when the row takes the full path or has nothing to correct.
@@ -258,9 +257,11 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
 // are shared out.
 template <typename DT, int VN>
 __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairArgs<DT> a) {
-    __shared__ TgtRow s_tg[kPairCap];
+    __shared__ TgtFast<DT> s_fa[kPairCap];
+    __shared__ TgtSlow s_sl[kPairCap];
     __shared__ int s_i, s_c;
     if (*a.err) return;
+    using U = typename Unsigned<DT>::T;
     constexpr int CW = kPairThreads * VN;
     const int n = a.n;
     const int nchunks = (n + CW - 1) / CW;
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
     __syncthreads();
     int i = s_i, c = s_c;
     int64_t wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
-    int cur = -1, s = -1, U = 0;
+    int cur = -1, s = -1, U_ = 0;
     for (;;) {
         if (c >= nchunks) {   // next row with items (block-uniform)
             do {
@@ -296,11 +297,13 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
         if (i != cur) {
             cur = i;
             s = a.rows[i];
-            U = (int)wc - 1;
+            U_ = (int)wc - 1;
             __syncthreads();   // the previous row's plan is no longer read
-            if (threadIdx.x < U) {
+            if (threadIdx.x < U_) {
                 const PairTgt p = a.plan[(size_t)s * a.tcap + threadIdx.x];
-                s_tg[threadIdx.x] = TgtRow{p.t, 0, p.dold, p.dnew, p.rold, p.rnew};
+                const size_t rt = (size_t)p.t * n;
+                s_fa[threadIdx.x] = TgtFast<DT>{a.D + rt, a.chg + (size_t)p.t * a.words, (DT)p.dold, (DT)p.dnew};
+                s_sl[threadIdx.x] = TgtSlow{(int64_t)rt, p.rold, p.rnew};
             }
             __syncthreads();
         }
@@ -322,32 +325,45 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
 #pragma unroll
         for (int q = 0; q < VN; ++q) acc[q] = ff{0.f, 0.f};
         unsigned any = 0;
-        for (int u = 0; u < U; ++u) {
-            const TgtRow& tg = s_tg[u];
-            const int64_t dold = tg.dold, dnew = tg.dnew;
-            const size_t rt = (size_t)tg.t * n;
+        const int wofs = x0 >> 5, bsh = x0 & 31;
+        for (int u = 0; u < U_; ++u) {
+            const TgtFast<DT> f = s_fa[u];
             DVec<DT, VN> dtn;
-            dtn.load(a.D + rt + x0);
-            const unsigned bt = chg_bits<VN>(a.chg, a.words, tg.t, x0);
+            dtn.load(f.Dt + x0);
+            const unsigned bt = (f.Ct[wofs] >> bsh) & ((1u << VN) - 1u);
             DVec<DT, VN> dto = dtn;
-            if (bt) patch_old<DT, VN>(dto, bt, a.oD + rt, x0);
-            const bool ho = dold >= 0 && any_sum<DT, VN>(dso, dto, dold);
-            const bool hn = dnew >= 0 && any_sum<DT, VN>(dsn, dtn, dnew);
-            if (!(ho | hn)) continue;
-            const unsigned mo = ho ? on_path<DT, VN>(dso, dto, dold) : 0u;
-            const unsigned mn = hn ? on_path<DT, VN>(dsn, dtn, dnew) : 0u;
+            if (bt) patch_old<DT, VN>(dto, bt, a.oD + (f.Dt - a.D), x0);
+            // any column on a path of either state (one add and compare each)
+            bool hit = false;
 #pragma unroll
             for (int q = 0; q < VN; ++q) {
-                const int x = x0 + q;
-                if ((mo >> q) & 1u) {
-                    const uint64_t ssx = ((bs >> q) & 1u) ? a.oS[rs + x] : a.S[rs + x];
-                    const uint64_t stx = ((bt >> q) & 1u) ? a.oS[rt + x] : a.S[rt + x];
-                    const ff t = pair_term(ssx, stx, tg.rold);
-                    acc[q] = ff_add(acc[q], ff{-t.hi, -t.lo});
-                }
-                if ((mn >> q) & 1u) acc[q] = ff_add(acc[q], pair_term(a.S[rs + x], a.S[rt + x], tg.rnew));
+                hit |= (U)dso.v[q] + (U)dto.v[q] == (U)f.dold;
+                hit |= (U)dsn.v[q] + (U)dtn.v[q] == (U)f.dnew;
             }
+            if (!hit) continue;
+            const unsigned mo = on_path<DT, VN>(dso, dto, (U)f.dold);
+            const unsigned mn = on_path<DT, VN>(dsn, dtn, (U)f.dnew);
             any |= mo | mn;
+            // one pass per matched column and state (a warp runs as many passes as its
+            // busiest lane has matches, usually one)
+            const TgtSlow& sl = s_sl[u];
+            const size_t rt = (size_t)sl.rt;
+            unsigned m = mo | (mn << VN);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const bool is_new = b >= VN;
+                const int q = is_new ? b - VN : b;
+                const int x = x0 + q;
+                const uint64_t ssx = (!is_new && ((bs >> q) & 1u)) ? a.oS[rs + x] : a.S[rs + x];
+                const uint64_t stx = (!is_new && ((bt >> q) & 1u)) ? a.oS[rt + x] : a.S[rt + x];
+                ff t = pair_term(ssx, stx, is_new ? sl.rnew : sl.rold);
+                if (!is_new) t = ff{-t.hi, -t.lo};
+                // acc[q] with a run-time q: select through the unrolled copies
+#pragma unroll
+                for (int j = 0; j < VN; ++j)
+                    if (j == q) acc[j] = ff_add(acc[j], t);
+            }
         }
 #pragma unroll
         for (int q = 0; q < VN; ++q)

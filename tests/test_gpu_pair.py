@@ -104,3 +104,32 @@ def test_pair_option_rejected_on_directed_graphs():
         a.bc_set_option("pair_updates", 1)
     assert e.value.code == binding.BC_ERR_ARG
     a.bc_set_option("pair_updates", 0)
+
+
+def _two_paths(n_each, w, w_join=None):
+    a = synth.path_graph(n_each, False, w)
+    src = np.concatenate([a.src, a.src + n_each]).astype(np.int32)
+    dst = np.concatenate([a.dst, a.dst + n_each]).astype(np.int32)
+    ww = np.concatenate([a.w, a.w]).astype(np.int64)
+    return synth.Graph(2 * n_each, False, src, dst, ww)
+
+
+def test_pair_joining_components_vector_columns():
+    # n a multiple of the column vector: joining two components turns INF pairs finite
+    g = _two_paths(32, 3)
+    ups = [("edge", 5, 40, 2), ("edge", 20, 60, 1), ("vertex", 33, [(1, 2, 0), (31, 4, 0)])]
+    _pair_vs_full(g, ups, "i32", "joining, n=64")
+
+
+def test_pair_large_distances():
+    # distances far above 16 bits, int64 state
+    g = synth.path_graph(64, False, 30000)
+    ups = [("edge", 0, 63, 5), ("edge", 10, 40, 7000)]
+    _pair_vs_full(g, ups, "i64", "distances above 16 bits")
+
+
+def test_pair_heavy_join():
+    # small distances until a heavy edge joins the two halves
+    g = _two_paths(32, 2)
+    ups = [("edge", 3, 7, 1), ("edge", 10, 50, 60000), ("edge", 12, 45, 3), ("edge", 0, 31, 1)]
+    _pair_vs_full(g, ups, "i32", "heavy join")
