@@ -668,6 +668,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
             return bail(e_ == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA,        \
                         std::string(#call) + ": " + cudaGetErrorString(e_));               \
     } while (0)
+    CKI(scan_setup());
     CKI(cudaMemsetAsync(d.err, 0, sizeof(int32_t), d.st));
     CKI(cudaMemsetAsync(d.stats, 0, 8 * sizeof(int64_t), d.st));
     CKI(cudaMemsetAsync(d.mark, 0, n, d.st));

@@ -246,6 +246,93 @@ __device__ __forceinline__ bool pair_rule(int64_t cand, int64_t old, size_t idx,
     return false;
 }
 
+// Quick test of the rank-1 rule on VN consecutive pairs (s, t .. t+VN-1) of row s with
+// distances dv and column distances cv: can any of them change?  (False positives only
+// cost time: scan_vec applies the exact rule.)
+// small: rd plus every finite column value stays below INF, so no finite sum can
+// overflow and a pair with d = INF and an INF column term cannot pass.
+template <typename DT>
+__device__ __forceinline__ bool quick_vec(const typename Vec<DT>::T& dv, const typename Vec<DT>::T& cv, int64_t rd,
+                                          bool small = false) {
+    using V = Vec<DT>;
+    constexpr int VN = V::N;
+    const int64_t INF = Inf<DT>::v;
+    bool any = false;
+    if constexpr (sizeof(DT) == 4) {
+        // both terms are below 2^31, so their sum fits 32 bits: a pair can change only if
+        // the sum does not exceed d (or d is INF, where a sum that does not fit must be
+        // reported).  An INF column term passes only where d is INF or rd is 0; the rule
+        // skips it.
+        const uint32_t r32 = (uint32_t)rd;
+        const int32_t* dp = reinterpret_cast<const int32_t*>(&dv);
+        const int32_t* cp = reinterpret_cast<const int32_t*>(&cv);
+        if (small) {
+#pragma unroll
+            for (int q = 0; q < VN; ++q) any |= r32 + (uint32_t)cp[q] <= (uint32_t)dp[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < VN; ++q) {
+                const uint32_t sum = r32 + (uint32_t)cp[q];
+                any |= (sum <= (uint32_t)dp[q]) | (dp[q] == INT32_MAX);
+            }
+        }
+    } else {
+        int64_t dd0[VN], cd0[VN];
+        V::unpack(dv, dd0);
+        V::unpack(cv, cd0);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) {
+            if (cd0[q] == INF) continue;
+            const int64_t cand = dsum<DT>(rd, cd0[q]);
+            any |= (cand <= dd0[q]) || (cand == SAT);
+        }
+    }
+    return any;
+}
+
+// The rank-1 rule on the VN consecutive pairs (s, t .. t+VN-1) of row s, given their
+// distances dv (updated in place) and the column distances cv; sigma is read only on
+// ties and written only where the pair changes.  Returns whether a distance changed
+// (dv must then be written back).
+template <typename DT>
+__device__ __forceinline__ bool rule_vec(const ScanArgs<DT>& a, int s, size_t rowoff, int t, typename Vec<DT>::T& dv,
+                                         const typename Vec<DT>::T& cv, int64_t rd, uint64_t rs, uint64_t rm,
+                                         int& n_changed, int& n_ties) {
+    using V = Vec<DT>;
+    constexpr int VN = V::N;
+    const int64_t INF = Inf<DT>::v;
+    int64_t dd[VN], cd[VN];
+    V::unpack(dv, dd);
+    V::unpack(cv, cd);
+    bool wr = false;
+#pragma unroll
+    for (int q = 0; q < VN; ++q) {
+        if (cd[q] == INF) continue;
+        const int64_t cand = dsum<DT>(rd, cd[q]);
+        int64_t nd;
+        const int ties0 = n_ties;
+        const uint64_t sig0 = a.rec.tcnt ? a.S[rowoff + t + q] : 0ull;
+        if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q], a.S, a.err, &nd,
+                          &n_ties)) {
+            V::set(dv, q, nd);
+            wr = true;
+            ++n_changed;
+            if (a.rec.tcnt) record_change<DT>(a.rec, a.n, s, t + q, dd[q], sig0);
+        } else if (n_ties != ties0 && a.rec.tcnt) {
+            record_change<DT>(a.rec, a.n, s, t + q, dd[q], sig0);
+        }
+    }
+    return wr;
+}
+
+template <typename DT>
+__device__ __forceinline__ bool scan_vec(const ScanArgs<DT>& a, int s, size_t rowoff, int t, typename Vec<DT>::T& dv,
+                                         const typename Vec<DT>::T& cv, int64_t rd, uint64_t rs, uint64_t rm,
+                                         int& n_changed, int& n_ties) {
+    if (!quick_vec<DT>(dv, cv, rd)) return false;
+    return rule_vec<DT>(a, s, rowoff, t, dv, cv, rd, rs, rm, n_changed, n_ties);
+}
+
 // One work item of the rank-1 pass: row s (scalars rd, rs, rm), chunk c of CW columns.
 template <typename DT, bool VECTOR>
 __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int64_t rd, uint64_t rs, uint64_t rm,
@@ -273,53 +360,8 @@ __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int6
         for (int u = 0; u < kScanUnroll; ++u) {
             const int t = t0 + (u * kScanThreads + tid) * VN;
             if (t >= n) break;
-            bool any = false;
-            if constexpr (sizeof(DT) == 4) {
-                // both terms are below 2^31, so their sum fits 32 bits: a pair can change
-                // only if the column term is finite and the sum does not exceed d (or d
-                // is INF, where a sum that does not fit must be reported)
-                const uint32_t r32 = (uint32_t)rd;
-                const int32_t* dp = reinterpret_cast<const int32_t*>(&dv[u]);
-                const int32_t* cp = reinterpret_cast<const int32_t*>(&cv[u]);
-#pragma unroll
-                for (int q = 0; q < VN; ++q) {
-                    const uint32_t sum = r32 + (uint32_t)cp[q];
-                    any |= (cp[q] != INT32_MAX) & ((sum <= (uint32_t)dp[q]) | (dp[q] == INT32_MAX));
-                }
-            } else {
-                int64_t dd0[VN], cd0[VN];
-                V::unpack(dv[u], dd0);
-                V::unpack(cv[u], cd0);
-#pragma unroll
-                for (int q = 0; q < VN; ++q) {
-                    if (cd0[q] == INF) continue;
-                    const int64_t cand = dsum<DT>(rd, cd0[q]);
-                    any |= (cand <= dd0[q]) || (cand == SAT);
-                }
-            }
-            if (!any) continue;
-            int64_t dd[VN], cd[VN];
-            V::unpack(dv[u], dd);
-            V::unpack(cv[u], cd);
-            bool wr = false;
-#pragma unroll
-            for (int q = 0; q < VN; ++q) {
-                if (cd[q] == INF) continue;
-                const int64_t cand = dsum<DT>(rd, cd[q]);
-                int64_t nd;
-                const int ties0 = n_ties;
-                const uint64_t sig0 = a.rec.tcnt ? a.S[rowoff + t + q] : 0ull;
-                if (pair_rule<DT>(cand, dd[q], rowoff + t + q, rs, rm, a.cS[t + q], a.cM[t + q],
-                                  a.S, a.err, &nd, &n_ties)) {
-                    V::set(dv[u], q, nd);
-                    wr = true;
-                    ++n_changed;
-                    if (a.rec.tcnt) record_change<DT>(a.rec, n, s, t + q, dd[q], sig0);
-                } else if (n_ties != ties0 && a.rec.tcnt) {
-                    record_change<DT>(a.rec, n, s, t + q, dd[q], sig0);
-                }
-            }
-            if (wr) *reinterpret_cast<typename V::T*>(Drow + t) = dv[u];
+            if (scan_vec<DT>(a, s, rowoff, t, dv[u], cv[u], rd, rs, rm, n_changed, n_ties))
+                *reinterpret_cast<typename V::T*>(Drow + t) = dv[u];
         }
     } else {
         for (int t = t0 + tid; t < t0 + CW && t < n; t += kScanThreads) {

@@ -210,6 +210,7 @@ __device__ __forceinline__ void record_change(const PairRec& r, int n, int s, in
 }
 
 // ---- launches (k_update.cu) ----
+cudaError_t scan_setup();
 void launch_estar_write(const Dev& d, const EOps& ops);
 void launch_estar_move(const Dev& d, const EMoves& moves);
 void launch_alg4_in(const Dev& d, int32_t v, const VEdge* e, int32_t k);

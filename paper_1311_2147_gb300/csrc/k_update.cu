@@ -126,6 +126,121 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
 
 // Row v <- the OUT phase's result; with rec.tcnt set, the pairs (v,t) whose distance or
 // path count changes are recorded.
+// K2, vector path (n a multiple of the vector width).  Work item = (chunk c of CW
+// columns, row i) in chunk-major order, so the column vector of a chunk is staged in
+// shared memory (with its largest finite value) once for all the rows a CTA meets in
+// that chunk; CTAs take items in turn.  Each thread issues the kScanVecs 16-byte loads
+// of its part of the row chunk before using any (the row of the next item is fetched a
+// step ahead, so these loads do not wait for it), then applies the quick test of the
+// rule to every vector and the rule itself (scan_vec) to the rare vectors that can
+// change.  Changed vectors are written back to D.  (Measured alternatives: a bulk-copy
+// (TMA) pipeline with 2-6 stages of 16 KB per CTA and a contiguous block of items per
+// CTA were both slower on this pass.)
+constexpr int kScanVecs = 8;
+constexpr int kScanCtasPerSm = 3;
+
+template <typename DT>
+__global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm) k_scan_cm(ScanArgs<DT> a) {
+    using V = Vec<DT>;
+    constexpr int VN = V::N;
+    constexpr int CW = kScanThreads * VN * kScanVecs;
+    extern __shared__ __align__(16) unsigned char smem[];
+    DT* scd = reinterpret_cast<DT*>(smem);   // CW column values
+    if (block_err(a.err)) return;
+    const int tid = threadIdx.x;
+    const int n = a.n;
+    const int64_t INF = Inf<DT>::v;
+    const int cnt = *a.count;
+    const int nchunks = (n + CW - 1) / CW;
+    const int total = cnt * nchunks;   // at most 32768 rows x 16 chunks
+    if (blockIdx.x == 0 && tid == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6), (unsigned long long)cnt);
+    int n_changed = 0, n_ties = 0;
+    {
+        // CTAs take items in turn (item = block + k * grid): at any moment the CTAs
+        // read neighbouring rows, which keeps the DRAM accesses of the whole grid local
+        __shared__ int64_t s_cmax;
+        int64_t cmax = 0;
+        int cur_c = -1;
+        int item = blockIdx.x;
+        // the row of the next item is fetched one item ahead, so the loads of D do not
+        // wait for it
+        int s_next = item < total ? a.rows[item - (item / cnt) * cnt] : 0;
+        for (; item < total; item += gridDim.x) {
+            const int c = item / cnt;
+            const int t0 = c * CW;
+            const int s = s_next;
+            if (item + (int)gridDim.x < total) {
+                const int nx = item + gridDim.x;
+                s_next = a.rows[nx - (nx / cnt) * cnt];
+            }
+            if (c != cur_c) {   // block-uniform: stage the column chunk and its largest finite value
+                cur_c = c;
+                __syncthreads();   // the previous chunk is no longer read
+                if (tid == 0) s_cmax = 0;
+                __syncthreads();
+                int64_t m = 0;
+#pragma unroll
+                for (int u = 0; u < kScanVecs; ++u) {
+                    const int j = (u * kScanThreads + tid) * VN;
+                    if (t0 + j < n) {
+                        const typename V::T x = __ldg(reinterpret_cast<const typename V::T*>(a.cD + t0 + j));
+                        *reinterpret_cast<typename V::T*>(scd + j) = x;
+                        int64_t xv[VN];
+                        V::unpack(x, xv);
+#pragma unroll
+                        for (int q = 0; q < VN; ++q)
+                            if (xv[q] != INF && xv[q] > m) m = xv[q];
+                    }
+                }
+                atomicMax(reinterpret_cast<unsigned long long*>(&s_cmax), (unsigned long long)m);
+                __syncthreads();
+                cmax = s_cmax;
+            }
+            const int64_t rd = (s == a.skip_row) ? INF : (int64_t)a.fD[s];
+            if (rd != INF) {
+                const size_t rowoff = (size_t)s * n;
+                DT* Drow = a.D + rowoff;
+                typename V::T dv[kScanVecs];
+#pragma unroll
+                for (int u = 0; u < kScanVecs; ++u) {
+                    const int t = t0 + (u * kScanThreads + tid) * VN;
+                    if (t < n) dv[u] = __ldcs(reinterpret_cast<const typename V::T*>(Drow + t));
+                }
+                // quick test of every vector first; the rare vectors that can change are
+                // read again (from cache) by a loop that is not unrolled, so the rule's
+                // code does not hold the registers of all kScanVecs vectors.  When no
+                // finite sum of the row can exceed a finite distance bound (rd + the
+                // chunk's largest finite column value < INF), the test is one add and
+                // compare per pair.
+                const bool small = rd + cmax < INF;
+                unsigned cand = 0;
+#pragma unroll
+                for (int u = 0; u < kScanVecs; ++u) {
+                    const int j = (u * kScanThreads + tid) * VN;
+                    if (t0 + j >= n) break;
+                    const typename V::T cv = *reinterpret_cast<const typename V::T*>(scd + j);
+                    if (quick_vec<DT>(dv[u], cv, rd, small)) cand |= 1u << u;
+                }
+                if (cand) {
+                    const uint64_t rs = a.fS[s], rm = a.fM[s];
+                    while (cand) {
+                        const int u = __ffs(cand) - 1;
+                        cand &= cand - 1;
+                        const int j = (u * kScanThreads + tid) * VN;
+                        const int t = t0 + j;
+                        typename V::T d1 = *reinterpret_cast<const typename V::T*>(Drow + t);
+                        const typename V::T cv = *reinterpret_cast<const typename V::T*>(scd + j);
+                        if (rule_vec<DT>(a, s, rowoff, t, d1, cv, rd, rs, rm, n_changed, n_ties))
+                            *reinterpret_cast<typename V::T*>(Drow + t) = d1;
+                    }
+                }
+            }
+        }
+    }
+    scan_stats(a.stats, n_changed, n_ties);
+}
+
 template <typename DT>
 __global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, const uint64_t* cS, PairRec rec,
                             const int32_t* err) {
@@ -206,14 +321,30 @@ void launch_compact(const Dev& d, const uint8_t* mark, int clear, int32_t* rows,
                                                full, stats ? d.stats : nullptr, d.err);
 }
 
+// Dynamic shared memory of k_scan_cm: one chunk of the column vector.
+template <typename DT>
+static constexpr size_t scan_cm_smem() {
+    return (size_t)kScanThreads * Vec<DT>::N * kScanVecs * sizeof(DT);
+}
+
+// Allows k_scan_cm its shared memory on the current device.
+cudaError_t scan_setup() {
+    cudaError_t e = cudaFuncSetAttribute(k_scan_cm<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)scan_cm_smem<int32_t>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scan_cm<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)scan_cm_smem<int64_t>());
+    return e;
+}
+
 template <typename DT>
 static void scan_dispatch(const Dev& d, ScanArgs<DT> a) {
-    const int grid = d.nsm * 8;
     constexpr int VN = Vec<DT>::N;
-    if (d.n % VN == 0)
-        k_scan<DT, true><<<grid, kScanThreads, 0, d.st>>>(a);
-    else
-        k_scan<DT, false><<<grid, kScanThreads, 0, d.st>>>(a);
+    if (d.n % VN == 0) {
+        k_scan_cm<DT><<<d.nsm * kScanCtasPerSm, kScanThreads, scan_cm_smem<DT>(), d.st>>>(a);
+    } else {
+        k_scan<DT, false><<<d.nsm * 8, kScanThreads, 0, d.st>>>(a);
+    }
 }
 
 template <typename DT>
