@@ -190,18 +190,22 @@ struct PairRec {
     int32_t* tcnt;       // NULL: nothing is recorded
     int32_t* tlist;
     int32_t tcap;
+    int32_t first;       // no pair has changed yet in this update (the IN phase; row v)
 };
 
 // The first change of pair (s,t) in an update sets its bit, saves its old distance and
 // path count, and lists t as a changed target of row s (targets beyond the capacity
 // are only counted).  Later changes of the same pair (the OUT phase after the IN
-// phase) keep the saved values.
+// phase) keep the saved values.  Each pair is written by one thread per pass, and a
+// bit set by an earlier pass is visible, so a plain read of the word decides; the bit
+// is then set without waiting for the old word.
 template <typename DT>
 __device__ __forceinline__ void record_change(const PairRec& r, int n, int s, int t, int64_t d_old,
                                               uint64_t sig_old) {
     const uint32_t bit = 1u << (t & 31);
-    const uint32_t prev = atomicOr(r.chg + (size_t)s * r.chg_words + (t >> 5), bit);
-    if (prev & bit) return;
+    uint32_t* w = r.chg + (size_t)s * r.chg_words + (t >> 5);
+    if (!r.first && (*w & bit)) return;
+    atomicOr(w, bit);
     const size_t i = (size_t)s * n + t;
     static_cast<DT*>(r.oldD)[i] = (DT)d_old;
     r.oldS[i] = sig_old;

@@ -385,6 +385,7 @@ PairRec pair_rec(const Dev& d) {
     r.tcnt = d.tcnt;
     r.tlist = d.tlist;
     r.tcap = d.tcap;
+    r.first = 0;
     return r;
 }
 

@@ -163,16 +163,20 @@ __global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm) k_scan_cm(ScanAr
         int64_t cmax = 0;
         int cur_c = -1;
         int item = blockIdx.x;
-        // the row of the next item is fetched one item ahead, so the loads of D do not
-        // wait for it
+        // the row of the next item and its distance to v are fetched one item ahead, so
+        // the loads of D do not wait for them
+        auto rd_of = [&](int r) { return (r == a.skip_row) ? INF : (int64_t)a.fD[r]; };
         int s_next = item < total ? a.rows[item - (item / cnt) * cnt] : 0;
+        int64_t rd_next = item < total ? rd_of(s_next) : INF;
         for (; item < total; item += gridDim.x) {
             const int c = item / cnt;
             const int t0 = c * CW;
             const int s = s_next;
+            const int64_t rd = rd_next;
             if (item + (int)gridDim.x < total) {
                 const int nx = item + gridDim.x;
                 s_next = a.rows[nx - (nx / cnt) * cnt];
+                rd_next = rd_of(s_next);
             }
             if (c != cur_c) {   // block-uniform: stage the column chunk and its largest finite value
                 cur_c = c;
@@ -197,7 +201,6 @@ __global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm) k_scan_cm(ScanAr
                 __syncthreads();
                 cmax = s_cmax;
             }
-            const int64_t rd = (s == a.skip_row) ? INF : (int64_t)a.fD[s];
             if (rd != INF) {
                 const size_t rowoff = (size_t)s * n;
                 DT* Drow = a.D + rowoff;
@@ -327,7 +330,7 @@ static constexpr size_t scan_cm_smem() {
     return (size_t)kScanThreads * Vec<DT>::N * kScanVecs * sizeof(DT);
 }
 
-// Allows k_scan_cm its shared memory on the current device.
+// Allows the vector-path kernels their shared memory on the current device.
 cudaError_t scan_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_scan_cm<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)scan_cm_smem<int32_t>());
@@ -365,16 +368,19 @@ static ScanArgs<DT> scan_args(const Dev& d) {
     return a;
 }
 
-// IN phase: columns come from row v of the state (unchanged during this phase).
+// IN phase: columns come from row v of the state (unchanged during this phase).  It is
+// the first pass of an update that writes pairs.
 void launch_scan_in(const Dev& d, int32_t v) {
     if (d.dbytes == 4) {
         ScanArgs<int32_t> a = scan_args<int32_t>(d);
+        a.rec.first = 1;
         a.cD = (const int32_t*)d.D + (size_t)v * d.n;
         a.cS = d.S + (size_t)v * d.n;
         a.cM = a.cS;
         scan_dispatch<int32_t>(d, a);
     } else {
         ScanArgs<int64_t> a = scan_args<int64_t>(d);
+        a.rec.first = 1;
         a.cD = (const int64_t*)d.D + (size_t)v * d.n;
         a.cS = d.S + (size_t)v * d.n;
         a.cM = a.cS;
@@ -402,15 +408,17 @@ void launch_scan_out(const Dev& d, int32_t v) {
     }
 }
 
+// Row v is never written before this in an update (Lemma 1 in the IN phase; the OUT
+// phase's pass skips it), so its changes are first changes.
 void launch_write_row(const Dev& d, int32_t v) {
+    PairRec rec = d.pair_on ? pair_rec(d) : PairRec{};
+    rec.first = 1;
     if (d.dbytes == 4)
         k_write_row<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int32_t*)d.D, d.S, v,
-                                                                (const int32_t*)d.cD, d.cS,
-                                                                d.pair_on ? pair_rec(d) : PairRec{}, d.err);
+                                                                (const int32_t*)d.cD, d.cS, rec, d.err);
     else
         k_write_row<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int64_t*)d.D, d.S, v,
-                                                                (const int64_t*)d.cD, d.cS,
-                                                                d.pair_on ? pair_rec(d) : PairRec{}, d.err);
+                                                                (const int64_t*)d.cD, d.cS, rec, d.err);
 }
 
 void launch_estar_keep(const Dev& d, uint8_t* keep) {
