@@ -50,6 +50,19 @@ def load_peaks():
     return PEAKS_FALLBACK["hbm_gbs"], "fallback"
 
 
+def int_alu_peak():
+    """Integer ALU peak in Tops/s: SMs x 128 int32 lanes per SM x the maximum SM clock
+    (MEASURED_PEAKS.json's sm_max_mhz, else the nominal 2070 MHz)."""
+    import torch
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * mhz * 1e6 / 1e12
+
+
 def workload(name: str):
     from paper_1311_2147_gb300 import synth
     if name == "ba16384":
@@ -122,11 +135,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def read_traffic(kernel_class: str, workload_name: str):
-    """DRAM bytes per launch from the committed ncu summary of this kernel, if the kernel
-    source is unchanged since it was captured (else None)."""
+def read_traffic(profile_name: str, units_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary profiles/<profile_name>.md:
+    its measured bytes per unit of work (captured on a smaller case of the same kernel)
+    times the units one launch of this run processes.  None when the kernel source
+    changed since the capture (its sha256 no longer matches) or there is no summary."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"{kernel_class}_{workload_name}.md")
+    path = os.path.join(ROOT, "profiles", f"{profile_name}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -137,12 +152,12 @@ def read_traffic(kernel_class: str, workload_name: str):
                 vals[k.strip()] = v.strip()
     src = vals.get("source_file")
     sha = vals.get("source_sha256")
-    if not src or not sha or "traffic_bytes_per_launch" not in vals:
+    if not src or not sha or "traffic_bytes_per_unit" not in vals:
         return None
     fp = os.path.join(ROOT, src)
     if not os.path.exists(fp) or hashlib.sha256(open(fp, "rb").read()).hexdigest() != sha:
         return None
-    return float(vals["traffic_bytes_per_launch"])
+    return float(vals["traffic_bytes_per_unit"]) * units_per_launch
 
 
 def cpu_oracle_rate(g, sample_sources: int, seed: int = 7):
@@ -258,35 +273,74 @@ def run_ours(args):
     prof = A.bc_get_profile(reset=True)
     infop1 = A.bc_get_info()
     A.bc_set_option("profile", 0)
-    d_rows_acc = infop1["rows_reaccumulated"] - infop0["rows_reaccumulated"]
-    d_rows_scan = infop1["rows_scanned"] - infop0["rows_scanned"]
-    d_low = infop1["pairs_lowered"] - infop0["pairs_lowered"]
-    d_tie = infop1["pairs_tied"] - infop0["pairs_tied"]
+    dinfo = {k: infop1[k] - infop0[k] for k in infop1 if isinstance(infop1[k], int)}
+    d_rows_acc, d_rows_scan = dinfo["rows_reaccumulated"], dinfo["rows_scanned"]
+    d_low, d_tie = dinfo["pairs_lowered"], dinfo["pairs_tied"]
+    d_full, d_pair_rows, d_pair_tgts = dinfo["rows_full"], dinfo["pair_rows"], dinfo["pair_targets"]
     # algorithmic HBM bytes per kernel class over the profiled steps
     alg_bytes = {
         # rank-1 pass: read d of every scanned pair, sigma read+write on ties, d+sigma
         # written where the distance drops
         "scan": d_rows_scan * n * sd + d_tie * 16 + d_low * (sd + 8),
-        # accumulation: per re-accumulated source its d row, sigma row and new delta row
-        "accumulate": d_rows_acc * n * (sd + 8 + 8),
+        # accumulation (the rows over the target cap): d row, sigma row, new delta row
+        "accumulate": d_full * n * (sd + 8 + 8),
         # BC row sums: the changed delta rows are read twice (before and after)
         "bc_rows": 2 * d_rows_acc * n * 8,
     }
+    # pair corrections: per (row, changed target, column) one add and one compare for
+    # each of the two states (integer ALU work; the rows come from L2)
+    alu_ops = {"pair_corrections": 4 * d_pair_tgts * n}
     peak, peak_kind = load_peaks()
+    int_peak = int_alu_peak()
     dom = max(prof, key=lambda c: prof[c][0])
     dom_ms, dom_launches = prof[dom]
     roof = None
-    if dom in alg_bytes and dom_launches > 0 and dom_ms > 0:
+    if dom in alu_ops and dom_ms > 0 and dom_launches > 0:
+        kl = dom_launches // 3 or 1   # k_pair_plan, k_pair_weights, k_pairdep per update
+        achieved = alu_ops[dom] / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel_class": dom, "kernel": "k_pairdep (with k_pair_plan, k_pair_weights)",
+                "achieved": achieved, "peak": int_peak, "unit": "Tops/s (int32)", "frac": achieved / int_peak,
+                "peak_kind": "derived: SMs x 128 int32 lanes x max SM clock",
+                "alg_ops_per_launch": alu_ops[dom] / kl,
+                "traffic": read_traffic("pair_corrections_ba8192", d_pair_rows * n / kl),
+                "launches": kl, "avg_launch_ms": dom_ms / kl}
+    elif dom in alg_bytes and dom_launches > 0 and dom_ms > 0:
         per_launch = alg_bytes[dom] / dom_launches
         achieved = alg_bytes[dom] / (dom_ms / 1e3) / 1e9
-        traffic = read_traffic(dom, args.workload)
         roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "alg_bytes_per_launch": per_launch, "traffic": traffic,
+                "alg_bytes_per_launch": per_launch, "traffic": None,
                 "launches": dom_launches, "avg_launch_ms": dom_ms / dom_launches}
     classes = {c: {"ms": prof[c][0], "launches": prof[c][1],
                    "gbs": (alg_bytes[c] / (prof[c][0] / 1e3) / 1e9) if c in alg_bytes and prof[c][0] > 0 else None}
                for c in prof}
+
+    # ---------------- the n x n update kernel over every row (the paper's all-pairs
+    # Step 2), on the same state: HBM roofline of the rank-1 pass
+    roof_scan = None
+    extra = ups[(W + 2 * K) * U:(W + 2 * K) * U + 8]
+    if extra:
+        A.bc_set_option("full_scan", 1)
+        A.bc_set_option("profile", 1)
+        A.bc_get_profile(reset=True)
+        i0 = A.bc_get_info()
+        rc, _ = A.bc_apply_updates(extra)
+        assert rc == 0, A.last_error()
+        pf = A.bc_get_profile(reset=True)
+        i1 = A.bc_get_info()
+        A.bc_set_option("profile", 0)
+        A.bc_set_option("full_scan", 0)
+        ms, nl = pf["scan"]
+        rows = i1["rows_scanned"] - i0["rows_scanned"]
+        b = rows * n * sd + (i1["pairs_tied"] - i0["pairs_tied"]) * 16 + \
+            (i1["pairs_lowered"] - i0["pairs_lowered"]) * (sd + 8)
+        if ms > 0 and nl > 0:
+            achieved = b / (ms / 1e3) / 1e9
+            roof_scan = {"bound": "hbm", "kernel": "k_scan_cm, every row (full pass)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": b / nl,
+                         "traffic": read_traffic("scan_ba8192_fullscan", rows * n / nl),
+                         "launches": nl, "avg_launch_ms": ms / nl, "updates": len(extra)}
     A.close()
 
     # ---------------- e2e through the C-ABI with host buffers, per-update latency
@@ -345,8 +399,8 @@ def run_ours(args):
     if rank == 0:
         rows_per_upd = (info1["rows_reaccumulated"] - info0["rows_reaccumulated"]) / len(timed)
         per_update = {k: (info1[k] - info0[k]) / len(timed)
-                      for k in ("rows_reaccumulated", "rows_full", "rows_scanned", "pairs_lowered", "pairs_tied",
-                                "estar_moves", "estar_rebuilds")}
+                      for k in ("rows_reaccumulated", "rows_full", "pair_rows", "pair_targets", "rows_scanned",
+                                "pairs_lowered", "pairs_tied", "estar_moves", "estar_rebuilds")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int32/u64/f64" if dtype == "i32" else "int64/u64/f64", "data": "synthetic",
@@ -356,6 +410,7 @@ def run_ours(args):
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clk.summary(), "gpu_full_recompute": gpu_full,
                 "latency_ms": {"p50": e2e["p50_ms"], "p99": e2e["p99_ms"]} if e2e else None,
+                "roofline_scan": roof_scan,
                 "classes": classes, "rows_per_update": rows_per_upd, "per_update": per_update}
         print(json.dumps(line))
     if dist is not None:
@@ -527,8 +582,9 @@ def run_ncu_case(args):
         rc, _ = bg.bc_apply_updates([u])
         assert rc == 0, bg.last_error()
         after = bg.bc_get_info()
-        per_update.append({k: after[k] - before[k] for k in ("rows_reaccumulated", "rows_full", "rows_scanned",
-                                                             "pairs_lowered", "pairs_tied")})
+        per_update.append({k: after[k] - before[k] for k in ("rows_reaccumulated", "rows_full", "pair_rows",
+                                                             "pair_targets", "rows_scanned", "pairs_lowered",
+                                                             "pairs_tied")})
     print(json.dumps({"ncu_case": args.ncu_case, "n": g.n, "per_update": per_update, "info": bg.bc_get_info()}))
     return 0
 

@@ -117,6 +117,8 @@ typedef struct bc_info {
                                     corrected pair by pair ("pair_updates") */
     int64_t estar_rebuilds;      /* times the E* superset was laid out again (host round trip) */
     int64_t estar_moves;         /* vertex segments of E* moved to the free region instead */
+    int64_t pair_rows;           /* rows whose dependencies were corrected pair by pair */
+    int64_t pair_targets;        /* (row, changed target) pairs of those corrections */
 } bc_info;
 
 /*

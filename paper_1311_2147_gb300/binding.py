@@ -56,7 +56,8 @@ class bc_info(ctypes.Structure):
                 ("pairs_tied", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double),
                 ("rows_full", ctypes.c_int64), ("estar_rebuilds", ctypes.c_int64),
-                ("estar_moves", ctypes.c_int64)]
+                ("estar_moves", ctypes.c_int64), ("pair_rows", ctypes.c_int64),
+                ("pair_targets", ctypes.c_int64)]
 
 
 RESULT_DTYPE = np.dtype([("request_id", "<i8"), ("graph_id", "<i4"), ("status", "<i4"),

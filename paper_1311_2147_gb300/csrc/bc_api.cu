@@ -618,7 +618,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     if ((rc = dalloc(g, &d.S, nn)) || (rc = dalloc(g, &d.Dl, nn)) || (rc = dalloc(g, &d.bc_hi, n)) ||
         (rc = dalloc(g, &d.bc_lo, n)) || (rc = dalloc(g, &d.g_off, n + 1)) || (rc = dalloc(g, &d.g_src, arcs)) ||
         (rc = dalloc(g, &d.g_dst, arcs)) || (rc = dalloc(g, &d.e_off, n + 1)) || (rc = dalloc(g, &d.e_len, n)) ||
-        (rc = dalloc(g, &d.err, 1)) || (rc = dalloc(g, &d.stats, 8)) || (rc = dalloc(g, &d.mark, n)) ||
+        (rc = dalloc(g, &d.err, 1)) || (rc = dalloc(g, &d.stats, kStats)) || (rc = dalloc(g, &d.mark, n)) ||
         (rc = dalloc(g, &d.changed, n)) || (rc = dalloc(g, &d.rows, n)) || (rc = dalloc(g, &d.acc_rows, n)) ||
         (rc = dalloc(g, &d.counts, 8)) || (rc = dalloc(g, &d.fS, n)) || (rc = dalloc(g, &d.fM, n)) ||
         (rc = dalloc(g, &d.cS, n)) || (rc = dalloc(g, &d.cM, n)) ||
@@ -644,7 +644,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         d.pair_on = 1;
     }
     if (cudaMallocHost(&g->h_err, sizeof(int32_t)) != cudaSuccess ||
-        cudaMallocHost(&g->h_stats, 8 * sizeof(int64_t)) != cudaSuccess ||
+        cudaMallocHost(&g->h_stats, kStats * sizeof(int64_t)) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess ||
         (!dir && (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
                   cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -670,7 +670,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     } while (0)
     CKI(scan_setup());
     CKI(cudaMemsetAsync(d.err, 0, sizeof(int32_t), d.st));
-    CKI(cudaMemsetAsync(d.stats, 0, 8 * sizeof(int64_t), d.st));
+    CKI(cudaMemsetAsync(d.stats, 0, kStats * sizeof(int64_t), d.st));
     CKI(cudaMemsetAsync(d.mark, 0, n, d.st));
     CKI(cudaMemsetAsync(d.changed, 0, n, d.st));
     CKI(cudaMemsetAsync(d.counts, 0, 8 * sizeof(int32_t), d.st));
@@ -919,7 +919,7 @@ int bc_get_edges(bc_graph* g, int64_t* m, int32_t* src, int32_t* dst, int64_t* w
 int bc_get_info(bc_graph* g, bc_info* out) {
     if (!g || !out) return BC_ERR_ARG;
     CK(g, cudaStreamSynchronize(g->d.st));
-    CK(g, cudaMemcpy(g->h_stats, g->d.stats, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CK(g, cudaMemcpy(g->h_stats, g->d.stats, kStats * sizeof(int64_t), cudaMemcpyDeviceToHost));
     std::memset(out, 0, sizeof(*out));
     out->n = g->n;
     out->directed = g->directed ? 1 : 0;
@@ -934,6 +934,8 @@ int bc_get_info(bc_graph* g, bc_info* out) {
     out->pairs_tied = g->h_stats[5];
     out->rows_scanned = g->h_stats[6];
     out->rows_full = g->h_stats[7];
+    out->pair_rows = g->h_stats[8];
+    out->pair_targets = g->h_stats[9];
     out->estar_rebuilds = g->estar_rebuilds;
     out->estar_moves = g->estar_moves;
     out->kernel_launches = g->launches;

@@ -26,6 +26,12 @@ namespace bcg {
 
 enum : int32_t { ERRF_OVERFLOW = 1, ERRF_DIST = 2, ERRF_TIMEOUT = 4, ERRF_ARG_DEVICE = 8 };
 
+// Per-handle device counters: [0] rows re-accumulated [1] no-op updates [2] most rows of
+// one update [3] updates [4] pairs lowered [5] pairs with new tied paths [6] rows scanned
+// [7] rows re-accumulated in full [8] rows corrected pair by pair [9] (row, target) pairs
+// of those corrections.
+constexpr int kStats = 10;
+
 // Saturation marker for a distance sum that does not fit: INT64_MAX.  For DT =
 // int64 this equals INF, so callers test for it before comparing.
 constexpr int64_t SAT = INT64_MAX;

@@ -205,19 +205,27 @@ __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0
 
 // wpre[i] = total weight of the items of listed rows 0..i-1 (nchunks items per row);
 // one CTA, a block scan per tile of rows.
+// Also adds the rows with a correction and their targets to stats[8], stats[9].
 __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
                                                        const int32_t* tcnt, int tcap, int nchunks,
-                                                       int64_t* wpre, const int32_t* err) {
+                                                       int64_t* wpre, int64_t* stats, const int32_t* err) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total;
+    __shared__ int64_t s_rows[32], s_tgts[32];
     if (*err) return;
     const int cnt = *count;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = blockDim.x >> 5;
+    int64_t my_rows = 0, my_tgts = 0;
     int64_t base = 0;
     for (int tile = 0; tile < cnt; tile += blockDim.x) {
         const int i = tile + tid;
-        const int64_t w = i < cnt ? item_weight(tcnt[rows[i]], tcap) * nchunks : 0;
+        const int64_t iw = i < cnt ? item_weight(tcnt[rows[i]], tcap) : 0;
+        if (iw) {
+            ++my_rows;
+            my_tgts += iw - 1;
+        }
+        const int64_t w = iw * nchunks;
         int64_t incl = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -242,7 +250,26 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
         base += s_total;
         __syncthreads();
     }
-    if (tid == 0) wpre[cnt] = base;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_rows += __shfl_xor_sync(0xffffffffu, my_rows, o);
+        my_tgts += __shfl_xor_sync(0xffffffffu, my_tgts, o);
+    }
+    if (lane == 0) {
+        s_rows[wid] = my_rows;
+        s_tgts[wid] = my_tgts;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int64_t r = 0, t = 0;
+        for (int k = 0; k < nw; ++k) {
+            r += s_rows[k];
+            t += s_tgts[k];
+        }
+        wpre[cnt] = base;
+        stats[8] += r;
+        stats[9] += t;
+    }
 }
 
 // Work item = (listed row s, chunk of CW = threads x VN columns).  Each CTA owns an
@@ -427,7 +454,7 @@ void launch_pairdep(const Dev& d) {
     const int vn = (d.dbytes == 4) ? (d.n % 4 == 0 ? 4 : 1) : (d.n % 2 == 0 ? 2 : 1);
     const int cw = kPairThreads * vn;
     k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
-                                          d.pair_w, d.err);
+                                          d.pair_w, d.stats, d.err);
     const int grid = d.nsm * kPairCtasPerSm;   // one wave: the split of the work is static
     if (d.dbytes == 4) {
         if (vn == 4) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
