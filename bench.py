@@ -284,8 +284,11 @@ def run_ours(args):
         "scan": d_rows_scan * n * sd + d_tie * 16 + d_low * (sd + 8),
         # accumulation (the rows over the target cap): d row, sigma row, new delta row
         "accumulate": d_full * n * (sd + 8 + 8),
-        # BC row sums: the changed delta rows are read twice (before and after)
-        "bc_rows": 2 * d_rows_acc * n * 8,
+        # BC: the re-accumulated delta rows are read twice (before and after); with pair
+        # corrections only the full rows are, and per update the fixed-point column
+        # changes are read and BC (hi, lo) read and written (16 bytes each per column)
+        "bc_rows": (2 * d_full * n * 8 + len(prof_updates) * n * 48) if d_pair_rows
+        else 2 * d_rows_acc * n * 8,
     }
     # pair corrections: per (row, changed target, column) one add and one compare for
     # each of the two states (integer ALU work; the rows come from L2)

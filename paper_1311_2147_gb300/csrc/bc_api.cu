@@ -465,7 +465,9 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             launch_compact(d, d.mark, 1, d.full_rows, d.counts + 3, 0, 0);
         });
         timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
-        timed(g, 2, 2, [&] { launch_bc_rows(d, -1, 0); });
+        // BC: the full rows are subtracted before and added after their re-accumulation;
+        // the corrected rows add their changes to BC as they are made (k_pairdep)
+        timed(g, 2, 2, [&] { launch_bc_rows_list(d, -1, d.full_rows, d.counts + 3); });
         if (!g->profile) {
             // the two write disjoint dependency rows and only read the rest of the state:
             // the (latency-bound, often partial-wave) accumulation of the full rows runs
@@ -483,7 +485,10 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             timed(g, 5, 3, [&] { launch_pairdep(d); });
             timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
         }
-        timed(g, 2, 2, [&] { launch_bc_rows(d, +1, 0); });
+        timed(g, 2, 3, [&] {
+            launch_bc_rows_list(d, +1, d.full_rows, d.counts + 3);
+            launch_bc_fix(d);
+        });
         timed(g, 4, 1, [&] { launch_pair_clear(d); });
     } else {
         timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
@@ -636,7 +641,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
             (rc = dalloc(g, &d.chg, (size_t)n * d.chg_words)) || (rc = dalloc(g, &d.tcnt, n)) ||
             (rc = dalloc(g, &d.tlist, (size_t)n * kPairCap)) || (rc = dalloc(g, &d.full_rows, n)) ||
             (rc = dalloc(g, reinterpret_cast<uint8_t**>(&d.plan), (size_t)n * kPairCap * 40)) ||
-            (rc = dalloc(g, &d.pair_w, (size_t)n + 1))) {
+            (rc = dalloc(g, &d.pair_w, (size_t)n + 1)) || (rc = dalloc(g, &d.bcfix, 2 * (size_t)n))) {
             destroy_all(g);
             return fail(nullptr, rc, "device allocation failed");
         }
@@ -677,6 +682,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     if (!dir) {
         CKI(cudaMemsetAsync(d.chg, 0, sizeof(uint32_t) * n * d.chg_words, d.st));
         CKI(cudaMemsetAsync(d.tcnt, 0, sizeof(int32_t) * n, d.st));
+        CKI(cudaMemsetAsync(d.bcfix, 0, sizeof(int64_t) * 2 * n, d.st));
     }
     CKI(cudaStreamSynchronize(d.st));
     CKI(cudaEventRecord(e0, d.st));

@@ -177,6 +177,8 @@ struct Dev {
     void* plan;          // [n * tcap] per-target scalars of the pair corrections (k_pair.cu)
     int64_t* pair_w;     // [n + 1] prefix of the pair corrections' work item weights
     int32_t* full_rows;  // [n] rows re-accumulated in full (counts[3])
+    int64_t* bcfix;      // [2n] BC change of the corrected rows in this update, per column a
+                         // fixed-point pair (units of 2^-24, units of 2^-56); zero between updates
     cudaStream_t st;
 };
 
@@ -236,11 +238,13 @@ PairRec pair_rec(const Dev& d);
 void launch_full_flags(const Dev& d);
 void launch_pairdep(const Dev& d);
 void launch_pair_clear(const Dev& d);
+void launch_bc_fix(const Dev& d);
 
 // ---- launches (k_accum.cu) ----
 void launch_accum(const Dev& d, int is_static);
 void launch_accum_rows(const Dev& d, const int32_t* rows, const int32_t* count);
 void launch_bc_rows(const Dev& d, int sign, int is_static);
+void launch_bc_rows_list(const Dev& d, int sign, const int32_t* rows, const int32_t* count);
 
 // ---- launches (k_static.cu) ----
 void launch_sssp(const Dev& d);

@@ -174,18 +174,26 @@ void launch_accum_rows(const Dev& d, const int32_t* rows, const int32_t* count) 
 
 // sign = -1 / +1: subtract / add the rows listed in acc_rows; is_static: all rows,
 // overwriting BC.
-void launch_bc_rows(const Dev& d, int sign, int is_static) {
+static void bc_rows(const Dev& d, int sign, int is_static, const int32_t* rows, const int32_t* count) {
     const int tb = (d.n + 255) / 256;
     dim3 g1(tb, d.nrb_max);
-    const int32_t* rows = is_static ? nullptr : d.acc_rows;
     if (d.n % 2 == 0) {
         dim3 g2((d.n / 2 + 255) / 256, d.nrb_max);
-        k_bc_partial2<<<g2, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.Dl, d.partial, d.err);
+        k_bc_partial2<<<g2, 256, 0, d.st>>>(d.n, rows, count, d.Dl, d.partial, d.err);
     } else {
-        k_bc_partial<<<g1, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.Dl, d.partial, d.err);
+        k_bc_partial<<<g1, 256, 0, d.st>>>(d.n, rows, count, d.Dl, d.partial, d.err);
     }
-    k_bc_finish<<<tb, 256, 0, d.st>>>(d.n, rows, d.counts + 1, d.partial, (double)sign, is_static,
-                                      d.bc_hi, d.bc_lo, d.err);
+    k_bc_finish<<<tb, 256, 0, d.st>>>(d.n, rows, count, d.partial, (double)sign, is_static, d.bc_hi, d.bc_lo,
+                                      d.err);
+}
+
+void launch_bc_rows(const Dev& d, int sign, int is_static) {
+    bc_rows(d, sign, is_static, is_static ? nullptr : d.acc_rows, d.counts + 1);
+}
+
+// The same for the rows listed in rows[0..*count).
+void launch_bc_rows_list(const Dev& d, int sign, const int32_t* rows, const int32_t* count) {
+    bc_rows(d, sign, 0, rows, count);
 }
 
 }  // namespace bcg

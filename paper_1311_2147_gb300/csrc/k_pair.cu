@@ -80,8 +80,25 @@ struct PairArgs {
     const int32_t* rows;
     const int32_t* count;
     ff* Dl;
+    int64_t* bcfix;         // [2n] BC change of this update (fixed point, see bc_fix_add)
     int32_t* err;
 };
+
+// BC(x) += v for one corrected entry delta_s(x): v is added to the column's fixed-point
+// pair (A in units of 2^-24, B in units of 2^-56) by two integer atomics, so the total
+// does not depend on the order in which rows and CTAs add (the result is deterministic)
+// and is exact up to the 2^-57 rounding of each entry.  Bounds: each pair term
+// delta_st(x) lies in [0, 1] and a row has at most kPairCap targets, so |v| <= 128 and
+// |A| <= 2^31, |B| <= 2^31 per entry; a column receives at most one entry per row, so
+// for n < 2^21 both sums stay below 2^52 and k_bc_fix converts them exactly.
+__device__ __forceinline__ void bc_fix_add(int64_t* fix, int x, ff v) {
+    const double vd = ((double)v.hi + (double)v.lo) * 0x1p24;   // exact
+    const double a = rint(vd);
+    const long long b = __double2ll_rn((vd - a) * 0x1p32);       // vd - a is exact, |.| <= 1/2
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(fix + 2 * (size_t)x);
+    atomicAdd(p, (unsigned long long)(long long)a);
+    if (b) atomicAdd(p + 1, (unsigned long long)b);
+}
 
 // One CTA (kPlanThreads >= tcap threads) per listed row with 1..tcap changed targets:
 // sort them (the sums then run in a fixed order) and write the per-target scalars of
@@ -397,8 +414,32 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
             if ((any >> q) & 1u) {
                 ff* p = a.Dl + rs + x0 + q;
                 *p = ff_add(*p, acc[q]);
+                bc_fix_add(a.bcfix, x0 + q, acc[q]);
             }
     }
+}
+
+// BC (hi, lo) += the fixed-point change of each column, then the pair is zeroed for the
+// next update: B's high bits are carried into A (A' = A + (B >> 32), B' = B mod 2^32),
+// so A' * 2^-24 and B' * 2^-56 are exact doubles, added with TwoSum as in
+// dev_bc_finish.
+__global__ void k_bc_fix(int n, int64_t* fix, double* hi, double* lo, const int32_t* err) {
+    if (*err) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const longlong2 f = *reinterpret_cast<const longlong2*>(fix + 2 * (size_t)t);
+    if (f.x == 0 && f.y == 0) return;
+    *reinterpret_cast<longlong2*>(fix + 2 * (size_t)t) = make_longlong2(0, 0);
+    const long long A = f.x + (f.y >> 32);
+    const long long B = f.y & 0xFFFFFFFFll;
+    const double x1 = (double)A * 0x1p-24;
+    const double x2 = (double)B * 0x1p-56;
+    const double h = hi[t];
+    const double s = h + x1;
+    const double bp = s - h;
+    const double e = (h - (s - bp)) + (x1 - bp);
+    hi[t] = s;
+    lo[t] += e + x2;
 }
 
 // ------------------------------------------------------------------ launches
@@ -443,6 +484,7 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.rows = d.acc_rows;
     a.count = d.counts + 1;
     a.Dl = d.Dl;
+    a.bcfix = d.bcfix;
     a.err = d.err;
     return a;
 }
@@ -463,6 +505,10 @@ void launch_pairdep(const Dev& d) {
         if (vn == 2) k_pairdep<int64_t, 2><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
         else k_pairdep<int64_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
     }
+}
+
+void launch_bc_fix(const Dev& d) {
+    k_bc_fix<<<(d.n + 255) / 256, 256, 0, d.st>>>(d.n, d.bcfix, d.bc_hi, d.bc_lo, d.err);
 }
 
 }  // namespace bcg
