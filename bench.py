@@ -208,6 +208,22 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest x over all ranks of the process group (x itself on one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, t_max_s: float) -> float:
+    """Whole-job throughput of replicas with the same work per rank: every rank's units
+    over the slowest rank's time."""
+    return world * units_per_rank / t_max_s
+
+
 def run_ours(args):
     import torch
     from paper_1311_2147_gb300 import binding, synth
@@ -256,12 +272,8 @@ def run_ours(args):
     dev_ms = e0.elapsed_time(e1)
     info1 = A.bc_get_info()
     launches = info1["kernel_launches"] - info0["kernel_launches"]
-    t_max = dev_ms
-    if dist is not None:
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * len(timed) / (t_max / 1e3)
+    t_max = max_over_ranks(dev_ms, dist)
+    value = job_rate(len(timed), world, t_max / 1e3)
 
     # ---------------- per-kernel-class profile over the next K steps (events per launch)
     A.bc_set_option("profile", 1)
@@ -370,12 +382,8 @@ def run_ours(args):
             scores = B.bc_get_scores()
             d2h += 2 * scores.nbytes
         barrier()
-        wall = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([wall], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
-        e2e = {"value": world * len(timed) / wall, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
+        wall = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": job_rate(len(timed), world, wall), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                "d2h_bytes_per_step": d2h // K, "p50_ms": float(np.percentile(lat, 50)),
                "p99_ms": float(np.percentile(lat, 99))}
         B.close()

@@ -56,8 +56,10 @@ __device__ __forceinline__ ff ff_shfl_xor(ff x, int o) {
 
 // A path count as a float-float: the value is cut into 20 + 22 + 22 bits, each of which
 // converts to fp32 exactly, and the three are summed (exact up to 48 significant bits,
-// rounded in the low part beyond that).
+// rounded in the low part beyond that).  A count below 2^24 is one exact fp32 value,
+// which is also what the three-part sum gives for it.
 __device__ __forceinline__ ff ff_from_u64(uint64_t v) {
+    if (v < (1ull << 24)) return ff{__uint2float_rn((uint32_t)v), 0.0f};
     const float c2 = __uint2float_rn((uint32_t)(v >> 44)) * 17592186044416.0f;          // 2^44
     const float c1 = __uint2float_rn((uint32_t)(v >> 22) & 0x3FFFFFu) * 4194304.0f;    // 2^22
     const float c0 = __uint2float_rn((uint32_t)v & 0x3FFFFFu);

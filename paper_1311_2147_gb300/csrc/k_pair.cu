@@ -27,6 +27,9 @@ namespace bcg {
 
 constexpr int kPairThreads = 256;
 constexpr int kPairCtasPerSm = 4;
+constexpr int kPairGroup = 2;   // targets whose rows are loaded together
+constexpr int kPairPieces = 8;  // pieces of equal weight per CTA of the grid
+constexpr int kPairVec32 = 4;   // columns per thread with int32 distances (4 or 8)
 
 // mark[s] = row s changed and has more recorded targets than the cap.
 __global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt, int tcap, uint8_t* mark) {
@@ -76,6 +79,7 @@ struct PairArgs {
     const int32_t* tlist;
     PairTgt* plan;          // [n * tcap]
     int64_t* wpre;          // [n + 1] prefix of the item weights of the listed rows
+    int32_t* next_piece;    // pieces of the work handed out so far past the first wave
     int tcap;
     const int32_t* rows;
     const int32_t* count;
@@ -150,7 +154,12 @@ template <typename DT, int VN>
 struct DVec {
     DT v[VN];
     __device__ __forceinline__ void load(const DT* p) {
-        if constexpr (VN == 4) {
+        if constexpr (VN == 8) {
+            const int4 x = *reinterpret_cast<const int4*>(p);
+            const int4 y = *reinterpret_cast<const int4*>(p + 4);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+        } else if constexpr (VN == 4) {
             const int4 x = *reinterpret_cast<const int4*>(p);
             v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
         } else if constexpr (VN == 2) {
@@ -225,7 +234,8 @@ __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0
 // Also adds the rows with a correction and their targets to stats[8], stats[9].
 __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
                                                        const int32_t* tcnt, int tcap, int nchunks,
-                                                       int64_t* wpre, int64_t* stats, const int32_t* err) {
+                                                       int64_t* wpre, int64_t* stats, int32_t* next_piece,
+                                                       const int32_t* err) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total;
     __shared__ int64_t s_rows[32], s_tgts[32];
@@ -284,138 +294,244 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
             t += s_tgts[k];
         }
         wpre[cnt] = base;
+        *next_piece = 0;
         stats[8] += r;
         stats[9] += t;
     }
 }
 
-// Work item = (listed row s, chunk of CW = threads x VN columns).  Each CTA owns an
-// equal share of the total item weight (wpre) and runs, in order, the items whose
-// start falls in it, so rows with many targets spread over several CTAs and there is
-// no tail of one heavy CTA.  The plan of a row is staged in shared memory when the CTA
-// meets the row.  Per target a thread loads row t at its VN columns once (the old
-// values differ only where the change map has a bit) and finds the columns on a
-// shortest s-t path with one add and compare per column and state (the rare matches
-// read path counts).  sum_t [delta'_st(x) - delta_st(x)] is added to delta_s(x) in the
-// plan's target order (old term first), so the result does not depend on how items
-// are shared out.
+// Queue of one warp's matches: entry = lane (5 bits) | q (3) | target index u (7) |
+// new state (1) | old d/sigma of s saved (1) | old d/sigma of t saved (1); the terms are
+// evaluated by all lanes together and summed by the owning lane in queue order.
+constexpr int kPairQueue = 64;
+struct PairQueue {
+    uint32_t e[kPairQueue];
+    ff term[kPairQueue];
+};
+
+// One work item: the VN columns x0 .. x0+VN-1 of this thread in row s, whose U_
+// targets are staged in s_fa / s_sl.  Targets go in groups of kPairGroup: the group's
+// rows are loaded together (one memory round trip), then tested with one add and
+// compare per column and state.  The matches (columns on a shortest s-t path of either
+// state) are appended to the warp's queue in target order, old state first; when the
+// queue is full and at the end of the item, the warp evaluates all queued terms at once
+// (one match per lane, its two path counts loaded together with the others) and each
+// lane adds its own terms to its column sums in queue order.  A column's sum thus runs
+// in target order whatever the lanes' loads are -- one column on the paths to every
+// target (a hub) no longer serialises its lane -- and does not depend on how the work
+// is shared out.
 template <typename DT, int VN>
-__global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairArgs<DT> a) {
-    __shared__ TgtFast<DT> s_fa[kPairCap];
-    __shared__ TgtSlow s_sl[kPairCap];
-    __shared__ int s_i, s_c;
-    if (*a.err) return;
+__device__ __forceinline__ void pair_item(const PairArgs<DT>& a, int s, int U_, int x0, const TgtFast<DT>* s_fa,
+                                          const TgtSlow* s_sl, ff (*s_acc)[kPairThreads], PairQueue& wq) {
+    static_assert(2 * VN * kPairGroup <= 32 && VN <= 8, "a group's matches fit one 32-bit mask");
     using U = typename Unsigned<DT>::T;
-    constexpr int CW = kPairThreads * VN;
+    constexpr unsigned kMask = (1u << VN) - 1u;
     const int n = a.n;
-    const int nchunks = (n + CW - 1) / CW;
-    const int cnt = *a.count;
-    const int64_t W = a.wpre[cnt];
-    const int64_t lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
-    if (lo >= hi) return;   // block-uniform
-    if (threadIdx.x == 0) {
-        // last row whose items start at or before lo: wpre[L] <= lo < wpre[R]
-        int L = 0, R = cnt;
-        while (R - L > 1) {
-            const int m = (L + R) >> 1;
-            if (a.wpre[m] <= lo) L = m; else R = m;
-        }
-        const int64_t wc = (a.wpre[L + 1] - a.wpre[L]) / nchunks;   // > 0: lo lies in row L
-        s_i = L;
-        s_c = (int)((lo - a.wpre[L] + wc - 1) / wc);
-    }
-    __syncthreads();
-    int i = s_i, c = s_c;
-    int64_t wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
-    int cur = -1, s = -1, U_ = 0;
-    for (;;) {
-        if (c >= nchunks) {   // next row with items (block-uniform)
-            do {
-                ++i;
-            } while (i < cnt && a.wpre[i + 1] == a.wpre[i]);
-            if (i >= cnt) break;
-            wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
-            c = 0;
-        }
-        if (a.wpre[i] + (int64_t)c * wc >= hi) break;
-        if (i != cur) {
-            cur = i;
-            s = a.rows[i];
-            U_ = (int)wc - 1;
-            __syncthreads();   // the previous row's plan is no longer read
-            if (threadIdx.x < U_) {
-                const PairTgt p = a.plan[(size_t)s * a.tcap + threadIdx.x];
-                const size_t rt = (size_t)p.t * n;
-                s_fa[threadIdx.x] = TgtFast<DT>{a.D + rt, a.chg + (size_t)p.t * a.words, (DT)p.dold, (DT)p.dnew};
-                s_sl[threadIdx.x] = TgtSlow{(int64_t)rt, p.rold, p.rnew};
-            }
-            __syncthreads();
-        }
-        const int x0 = c * CW + threadIdx.x * VN;
-        ++c;
-        if (x0 >= n) continue;
-        const size_t rs = (size_t)s * n;
-        DVec<DT, VN> dsn;
+    const int lane = threadIdx.x & 31;
+    const size_t rs = (size_t)s * n;
+    const bool active = x0 < n;   // the warp runs the item together (the queue needs every lane)
+    DVec<DT, VN> dsn, dso;
+    unsigned bs = 0;
+    if (active) {
         dsn.load(a.D + rs + x0);
-        const unsigned bs = chg_bits<VN>(a.chg, a.words, s, x0);
-        DVec<DT, VN> dso = dsn;
+        bs = chg_bits<VN>(a.chg, a.words, s, x0);
+        dso = dsn;
         if (bs) patch_old<DT, VN>(dso, bs, a.oD + rs, x0);
         if (s >= x0 && s < x0 + VN) {
 #pragma unroll
             for (int q = 0; q < VN; ++q)
                 if (x0 + q == s) dso.v[q] = dsn.v[q] = (DT)Inf<DT>::v;
         }
-        ff acc[VN];
+    }
+    unsigned any = 0;   // bit q: s_acc[q][tid] holds the sum of column x0 + q
+    int qlen = 0;       // warp-uniform
+    const int lane_x0 = x0 - lane * VN;   // column of lane 0's first vector
+    // evaluate the queued terms (all lanes), then add each lane's terms in queue order
+    auto flush = [&]() {
+        __syncwarp();
+        for (int e = lane; e < qlen; e += 32) {
+            const uint32_t en = wq.e[e];
+            const int L = en & 31, q = (en >> 5) & 7, u = (en >> 8) & 127;
+            const bool is_new = (en >> 15) & 1u;
+            const int x = lane_x0 + L * VN + q;
+            const TgtSlow& sl = s_sl[u];
+            const size_t rt = (size_t)sl.rt;
+            const uint64_t ssx = (!is_new && ((en >> 16) & 1u)) ? a.oS[rs + x] : a.S[rs + x];
+            const uint64_t stx = (!is_new && ((en >> 17) & 1u)) ? a.oS[rt + x] : a.S[rt + x];
+            ff t = pair_term(ssx, stx, is_new ? sl.rnew : sl.rold);
+            if (!is_new) t = ff{-t.hi, -t.lo};
+            wq.term[e] = t;
+        }
+        __syncwarp();
+        for (int e = 0; e < qlen; ++e) {
+            const uint32_t en = wq.e[e];
+            if ((int)(en & 31) == lane) {
+                const int q = (en >> 5) & 7;
+                const ff prev = ((any >> q) & 1u) ? s_acc[q][threadIdx.x] : ff{0.f, 0.f};
+                s_acc[q][threadIdx.x] = ff_add(prev, wq.term[e]);
+                any |= 1u << q;
+            }
+        }
+        __syncwarp();
+        qlen = 0;
+    };
+    const int wofs = x0 >> 5, bsh = x0 & 31;
+    for (int u0 = 0; u0 < U_; u0 += kPairGroup) {
+        DVec<DT, VN> dtg[kPairGroup];
+        unsigned btg[kPairGroup];
+        if (active) {
 #pragma unroll
-        for (int q = 0; q < VN; ++q) acc[q] = ff{0.f, 0.f};
-        unsigned any = 0;
-        const int wofs = x0 >> 5, bsh = x0 & 31;
-        for (int u = 0; u < U_; ++u) {
-            const TgtFast<DT> f = s_fa[u];
-            DVec<DT, VN> dtn;
-            dtn.load(f.Dt + x0);
-            const unsigned bt = (f.Ct[wofs] >> bsh) & ((1u << VN) - 1u);
+            for (int k = 0; k < kPairGroup; ++k)
+                if (u0 + k < U_) {
+                    const TgtFast<DT> f = s_fa[u0 + k];
+                    dtg[k].load(f.Dt + x0);
+                    btg[k] = f.Ct[wofs];
+                }
+        }
+        uint32_t mm = 0, btp = 0;
+#pragma unroll
+        for (int k = 0; k < kPairGroup; ++k) {
+            if (!active || u0 + k >= U_) break;
+            const TgtFast<DT> f = s_fa[u0 + k];
+            const DVec<DT, VN>& dtn = dtg[k];
+            const unsigned bt = (btg[k] >> bsh) & kMask;
             DVec<DT, VN> dto = dtn;
-            if (bt) patch_old<DT, VN>(dto, bt, a.oD + (f.Dt - a.D), x0);
-            // any column on a path of either state (one add and compare each)
             bool hit = false;
+            if (!(bs | bt)) {
+                // no saved values at these columns: the old and new sums are the same
 #pragma unroll
-            for (int q = 0; q < VN; ++q) {
-                hit |= (U)dso.v[q] + (U)dto.v[q] == (U)f.dold;
-                hit |= (U)dsn.v[q] + (U)dtn.v[q] == (U)f.dnew;
+                for (int q = 0; q < VN; ++q) {
+                    const U sum = (U)dsn.v[q] + (U)dtn.v[q];
+                    hit |= (sum == (U)f.dold) | (sum == (U)f.dnew);
+                }
+            } else {
+                if (bt) patch_old<DT, VN>(dto, bt, a.oD + (f.Dt - a.D), x0);
+#pragma unroll
+                for (int q = 0; q < VN; ++q) {
+                    hit |= (U)dso.v[q] + (U)dto.v[q] == (U)f.dold;
+                    hit |= (U)dsn.v[q] + (U)dtn.v[q] == (U)f.dnew;
+                }
             }
             if (!hit) continue;
             const unsigned mo = on_path<DT, VN>(dso, dto, (U)f.dold);
             const unsigned mn = on_path<DT, VN>(dsn, dtn, (U)f.dnew);
-            any |= mo | mn;
-            // one pass per matched column and state (a warp runs as many passes as its
-            // busiest lane has matches, usually one)
-            const TgtSlow& sl = s_sl[u];
-            const size_t rt = (size_t)sl.rt;
-            unsigned m = mo | (mn << VN);
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const bool is_new = b >= VN;
-                const int q = is_new ? b - VN : b;
-                const int x = x0 + q;
-                const uint64_t ssx = (!is_new && ((bs >> q) & 1u)) ? a.oS[rs + x] : a.S[rs + x];
-                const uint64_t stx = (!is_new && ((bt >> q) & 1u)) ? a.oS[rt + x] : a.S[rt + x];
-                ff t = pair_term(ssx, stx, is_new ? sl.rnew : sl.rold);
-                if (!is_new) t = ff{-t.hi, -t.lo};
-                // acc[q] with a run-time q: select through the unrolled copies
+            mm |= (mo | (mn << VN)) << (2 * VN * k);
+            btp |= bt << (VN * k);
+        }
+        // append this group's matches, each lane's in (target, state, q) order; a group
+        // that does not fit goes in parts, with a flush in between
+        while (__any_sync(0xffffffffu, mm != 0)) {
+            if (qlen == kPairQueue) flush();
+            const int cnt = __popc(mm);
+            int incl = cnt;
 #pragma unroll
-                for (int j = 0; j < VN; ++j)
-                    if (j == q) acc[j] = ff_add(acc[j], t);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            const int space = kPairQueue - qlen;
+            for (int pos = incl - cnt; mm && pos < space; ++pos) {
+                const int b = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const int k = b / (2 * VN), j = b - k * 2 * VN;
+                const unsigned is_new = j >= VN ? 1u : 0u;
+                const int q = is_new ? j - VN : j;
+                wq.e[qlen + pos] = (uint32_t)lane | ((uint32_t)q << 5) | ((uint32_t)(u0 + k) << 8) | (is_new << 15) |
+                                   (((bs >> q) & 1u) << 16) | (((btp >> (VN * k + q)) & 1u) << 17);
+            }
+            qlen += min(tot, space);
+            __syncwarp();
+        }
+    }
+    if (qlen) flush();
+#pragma unroll
+    for (int q = 0; q < VN; ++q)
+        if ((any >> q) & 1u) {
+            const ff acc = s_acc[q][threadIdx.x];
+            ff* p = a.Dl + rs + x0 + q;
+            *p = ff_add(*p, acc);
+            bc_fix_add(a.bcfix, x0 + q, acc);
+        }
+}
+
+// Work item = (listed row s, chunk of CW = threads x VN columns), in row-major order;
+// an item weighs the row's targets plus one.  The items are cut into kPairPieces x grid
+// pieces of equal weight (a piece runs the items whose start falls in it, so rows with
+// many targets spread over several pieces).  The first wave of CTAs takes the first
+// pieces and every CTA that finishes one takes the next from a counter: item costs
+// vary more than their weights (the matches, the per-item loads), and a static share
+// per CTA left half of the SMs idle for half of the kernel.  The plan of a row is
+// staged in shared memory when the CTA meets the row.
+template <typename DT, int VN>
+__global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairArgs<DT> a) {
+    __shared__ TgtFast<DT> s_fa[kPairCap];
+    __shared__ TgtSlow s_sl[kPairCap];
+    __shared__ ff s_acc[VN][kPairThreads];   // per thread: the sums of its VN columns
+    __shared__ PairQueue s_wq[kPairThreads / 32];
+    __shared__ int s_i, s_c, s_p;
+    if (*a.err) return;
+    constexpr int CW = kPairThreads * VN;
+    const int n = a.n;
+    const int nchunks = (n + CW - 1) / CW;
+    const int cnt = *a.count;
+    const int64_t W = a.wpre[cnt];
+    const int npieces = gridDim.x * kPairPieces;
+    int cur = -1, s = -1, U_ = 0;   // the row whose plan is staged
+    for (int piece = blockIdx.x; piece < npieces;) {
+        const int64_t lo = W * piece / npieces, hi = W * (piece + 1) / npieces;
+        if (lo < hi) {   // block-uniform
+            if (threadIdx.x == 0) {
+                // last row whose items start at or before lo: wpre[L] <= lo < wpre[R]
+                int L = 0, R = cnt;
+                while (R - L > 1) {
+                    const int m = (L + R) >> 1;
+                    if (a.wpre[m] <= lo) L = m; else R = m;
+                }
+                const int64_t wc = (a.wpre[L + 1] - a.wpre[L]) / nchunks;   // > 0: lo lies in row L
+                s_i = L;
+                s_c = (int)((lo - a.wpre[L] + wc - 1) / wc);
+            }
+            __syncthreads();
+            int i = s_i, c = s_c;
+            int64_t wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
+            for (;;) {
+                if (c >= nchunks) {   // next row with items (block-uniform)
+                    do {
+                        ++i;
+                    } while (i < cnt && a.wpre[i + 1] == a.wpre[i]);
+                    if (i >= cnt) break;
+                    wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
+                    c = 0;
+                }
+                if (a.wpre[i] + (int64_t)c * wc >= hi) break;
+                if (i != cur) {
+                    cur = i;
+                    s = a.rows[i];
+                    U_ = (int)wc - 1;
+                    __syncthreads();   // the previous row's plan is no longer read
+                    if (threadIdx.x < U_) {
+                        const PairTgt p = a.plan[(size_t)s * a.tcap + threadIdx.x];
+                        const size_t rt = (size_t)p.t * n;
+                        s_fa[threadIdx.x] =
+                            TgtFast<DT>{a.D + rt, a.chg + (size_t)p.t * a.words, (DT)p.dold, (DT)p.dnew};
+                        s_sl[threadIdx.x] = TgtSlow{(int64_t)rt, p.rold, p.rnew};
+                    }
+                    __syncthreads();
+                }
+                const int x0 = c * CW + threadIdx.x * VN;
+                ++c;
+                // a warp with at least one column in the row runs the item (all its lanes)
+                if (x0 - (int)(threadIdx.x & 31) * VN < n)
+                    pair_item<DT, VN>(a, s, U_, x0, s_fa, s_sl, s_acc, s_wq[threadIdx.x >> 5]);
             }
         }
-#pragma unroll
-        for (int q = 0; q < VN; ++q)
-            if ((any >> q) & 1u) {
-                ff* p = a.Dl + rs + x0 + q;
-                *p = ff_add(*p, acc[q]);
-                bc_fix_add(a.bcfix, x0 + q, acc[q]);
-            }
+        // the next piece: the first wave takes pieces 0 .. grid-1, later ones go in
+        // order to the CTAs that finish first
+        if (threadIdx.x == 0) s_p = gridDim.x + atomicAdd(a.next_piece, 1);
+        __syncthreads();
+        piece = s_p;
+        __syncthreads();   // s_p is read by all before thread 0 writes it again
     }
 }
 
@@ -480,6 +596,7 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.tlist = d.tlist;
     a.plan = reinterpret_cast<PairTgt*>(d.plan);
     a.wpre = d.pair_w;
+    a.next_piece = d.counts + 4;
     a.tcap = d.tcap;
     a.rows = d.acc_rows;
     a.count = d.counts + 1;
@@ -493,13 +610,14 @@ void launch_pairdep(const Dev& d) {
     const int pgrid = d.nsm * 8;
     if (d.dbytes == 4) k_pair_plan<int32_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int32_t>(d));
     else k_pair_plan<int64_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int64_t>(d));
-    const int vn = (d.dbytes == 4) ? (d.n % 4 == 0 ? 4 : 1) : (d.n % 2 == 0 ? 2 : 1);
+    const int vn = (d.dbytes == 4) ? (d.n % kPairVec32 == 0 ? kPairVec32 : 1) : (d.n % 2 == 0 ? 2 : 1);
     const int cw = kPairThreads * vn;
     k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
-                                          d.pair_w, d.stats, d.err);
-    const int grid = d.nsm * kPairCtasPerSm;   // one wave: the split of the work is static
+                                          d.pair_w, d.stats, d.counts + 4, d.err);
+    const int grid = d.nsm * kPairCtasPerSm;   // one resident wave; later pieces go to the first free CTA
     if (d.dbytes == 4) {
-        if (vn == 4) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
+        if (vn == 8) k_pairdep<int32_t, 8><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
+        else if (vn == 4) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
         else k_pairdep<int32_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
     } else {
         if (vn == 2) k_pairdep<int64_t, 2><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));

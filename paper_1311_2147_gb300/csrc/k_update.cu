@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
 // (TMA) pipeline with 2-6 stages of 16 KB per CTA and a contiguous block of items per
 // CTA were both slower on this pass.)
 constexpr int kScanVecs = 8;
-constexpr int kScanCtasPerSm = 3;
+constexpr int kScanCtasPerSm = 4;
 
 template <typename DT>
 __global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm) k_scan_cm(ScanArgs<DT> a) {
@@ -163,20 +163,23 @@ __global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm) k_scan_cm(ScanAr
         int64_t cmax = 0;
         int cur_c = -1;
         int item = blockIdx.x;
-        // the row of the next item and its distance to v are fetched one item ahead, so
-        // the loads of D do not wait for them
+        // the row of an item is fetched two items ahead and its distance to v one item
+        // ahead, so neither the loads of D nor the distance load wait for a load issued
+        // in the same item
         auto rd_of = [&](int r) { return (r == a.skip_row) ? INF : (int64_t)a.fD[r]; };
-        int s_next = item < total ? a.rows[item - (item / cnt) * cnt] : 0;
+        auto row_of = [&](int it) { return it < total ? a.rows[it - (it / cnt) * cnt] : 0; };
+        int s_next = row_of(item);
         int64_t rd_next = item < total ? rd_of(s_next) : INF;
+        int s_next2 = row_of(item + (int)gridDim.x);
         for (; item < total; item += gridDim.x) {
             const int c = item / cnt;
             const int t0 = c * CW;
             const int s = s_next;
             const int64_t rd = rd_next;
             if (item + (int)gridDim.x < total) {
-                const int nx = item + gridDim.x;
-                s_next = a.rows[nx - (nx / cnt) * cnt];
+                s_next = s_next2;
                 rd_next = rd_of(s_next);
+                s_next2 = row_of(item + 2 * (int)gridDim.x);
             }
             if (c != cur_c) {   // block-uniform: stage the column chunk and its largest finite value
                 cur_c = c;
