@@ -27,9 +27,11 @@ namespace bcg {
 
 constexpr int kPairThreads = 256;
 constexpr int kPairCtasPerSm = 4;
-constexpr int kPairGroup = 2;   // targets whose rows are loaded together
+// targets whose rows are loaded together: two with up to four columns per thread, one
+// with eight (whose two loads per target already overlap)
+template <int VN> struct PairGroup { static constexpr int value = VN >= 8 ? 1 : 2; };
 constexpr int kPairPieces = 8;  // pieces of equal weight per CTA of the grid
-constexpr int kPairVec32 = 4;   // columns per thread with int32 distances (4 or 8)
+constexpr int kPairVec32 = 8;   // columns per thread with int32 distances (4 or 8)
 
 // mark[s] = row s changed and has more recorded targets than the cap.
 __global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt, int tcap, uint8_t* mark) {
@@ -323,6 +325,7 @@ struct PairQueue {
 template <typename DT, int VN>
 __device__ __forceinline__ void pair_item(const PairArgs<DT>& a, int s, int U_, int x0, const TgtFast<DT>* s_fa,
                                           const TgtSlow* s_sl, ff (*s_acc)[kPairThreads], PairQueue& wq) {
+    constexpr int kPairGroup = PairGroup<VN>::value;
     static_assert(2 * VN * kPairGroup <= 32 && VN <= 8, "a group's matches fit one 32-bit mask");
     using U = typename Unsigned<DT>::T;
     constexpr unsigned kMask = (1u << VN) - 1u;
@@ -610,7 +613,9 @@ void launch_pairdep(const Dev& d) {
     const int pgrid = d.nsm * 8;
     if (d.dbytes == 4) k_pair_plan<int32_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int32_t>(d));
     else k_pair_plan<int64_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int64_t>(d));
-    const int vn = (d.dbytes == 4) ? (d.n % kPairVec32 == 0 ? kPairVec32 : 1) : (d.n % 2 == 0 ? 2 : 1);
+    // columns per thread: 16-byte (or two 16-byte) loads where n allows them
+    const int vn = (d.dbytes == 4) ? ((kPairVec32 == 8 && d.n % 8 == 0) ? 8 : (d.n % 4 == 0 ? 4 : 1))
+                                   : (d.n % 2 == 0 ? 2 : 1);
     const int cw = kPairThreads * vn;
     k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
                                           d.pair_w, d.stats, d.counts + 4, d.err);
