@@ -640,6 +640,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         if ((rc = dalloc(g, &poD, nn * (size_t)g->dbytes)) || (rc = dalloc(g, &d.oldS, nn)) ||
             (rc = dalloc(g, &d.chg, (size_t)n * d.chg_words)) || (rc = dalloc(g, &d.tcnt, n)) ||
             (rc = dalloc(g, &d.tlist, (size_t)n * kPairCap)) || (rc = dalloc(g, &d.full_rows, n)) ||
+            (rc = dalloc(g, &d.pair_rows, n)) ||
             (rc = dalloc(g, reinterpret_cast<uint8_t**>(&d.plan), (size_t)n * kPairCap * 40)) ||
             (rc = dalloc(g, &d.pair_w, (size_t)n + 1)) || (rc = dalloc(g, &d.bcfix, 2 * (size_t)n))) {
             destroy_all(g);

@@ -150,7 +150,8 @@ struct Dev {
     uint8_t* changed;    // [n] rows that changed in any phase of the current update
     int32_t* rows;       // [n] compacted rows of the current phase
     int32_t* acc_rows;   // [n] compacted rows to re-accumulate
-    int32_t* counts;     // [0] phase rows [1] accumulation rows [3] full rows
+    int32_t* counts;     // [0] phase rows [1] accumulation rows [3] full rows [4] pair pieces handed
+                         // out [5] rows corrected pair by pair
     void* fD;            // [n] per-row distance to v after the phase (DT)
     uint64_t* fS;        // [n] per-row path count to v after the phase
     uint64_t* fM;        // [n] per-row multiplier of a tie
@@ -177,6 +178,7 @@ struct Dev {
     void* plan;          // [n * tcap] per-target scalars of the pair corrections (k_pair.cu)
     int64_t* pair_w;     // [n + 1] prefix of the pair corrections' work item weights
     int32_t* full_rows;  // [n] rows re-accumulated in full (counts[3])
+    int32_t* pair_rows;  // [n] rows corrected pair by pair, most targets first (counts[5])
     int64_t* bcfix;      // [2n] BC change of the corrected rows in this update, per column a
                          // fixed-point pair (units of 2^-24, units of 2^-56); zero between updates
     cudaStream_t st;

@@ -82,6 +82,8 @@ struct PairArgs {
     PairTgt* plan;          // [n * tcap]
     int64_t* wpre;          // [n + 1] prefix of the item weights of the listed rows
     int32_t* next_piece;    // pieces of the work handed out so far past the first wave
+    const int32_t* prows;   // the rows corrected pair by pair, most targets first
+    const int32_t* pcount;
     int tcap;
     const int32_t* rows;
     const int32_t* count;
@@ -231,25 +233,56 @@ struct TgtSlow {
 // or 0 when the row takes the full path or has nothing to correct.
 __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0 || T > tcap) ? 0 : T + 1; }
 
-// wpre[i] = total weight of the items of listed rows 0..i-1 (nchunks items per row);
+// prows[0..*pcount) = the listed rows with 1..tcap targets, most targets first;
+// wpre[i] = total weight of the items of rows prows[0..i-1] (nchunks items per row);
 // one CTA, a block scan per tile of rows.
 // Also adds the rows with a correction and their targets to stats[8], stats[9].
 __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
                                                        const int32_t* tcnt, int tcap, int nchunks,
+                                                       int32_t* prows, int32_t* pcount,
                                                        int64_t* wpre, int64_t* stats, int32_t* next_piece,
                                                        const int32_t* err) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total;
     __shared__ int64_t s_rows[32], s_tgts[32];
+    __shared__ int s_hist[kPairCap + 1];
     if (*err) return;
-    const int cnt = *count;
+    const int cnt_all = *count;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = blockDim.x >> 5;
+    // the rows with 1..tcap targets, most targets first (a counting sort): the heaviest
+    // items are handed out first and the light ones fill the end of the kernel.  The
+    // order inside a bucket follows the atomics; a row's result does not depend on it.
+    for (int b = tid; b <= kPairCap; b += blockDim.x) s_hist[b] = 0;
+    __syncthreads();
+    for (int i = tid; i < cnt_all; i += blockDim.x) {
+        const int T = tcnt[rows[i]];
+        if (T > 0 && T <= tcap) atomicAdd(&s_hist[T], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int b = kPairCap; b >= 1; --b) {
+            const int h = s_hist[b];
+            s_hist[b] = acc;
+            acc += h;
+        }
+        s_hist[0] = acc;
+        *pcount = acc;
+    }
+    __syncthreads();
+    const int cnt = s_hist[0];
+    for (int i = tid; i < cnt_all; i += blockDim.x) {
+        const int r = rows[i];
+        const int T = tcnt[r];
+        if (T > 0 && T <= tcap) prows[atomicAdd(&s_hist[T], 1)] = r;
+    }
+    __syncthreads();
     int64_t my_rows = 0, my_tgts = 0;
     int64_t base = 0;
     for (int tile = 0; tile < cnt; tile += blockDim.x) {
         const int i = tile + tid;
-        const int64_t iw = i < cnt ? item_weight(tcnt[rows[i]], tcap) : 0;
+        const int64_t iw = i < cnt ? item_weight(tcnt[prows[i]], tcap) : 0;
         if (iw) {
             ++my_rows;
             my_tgts += iw - 1;
@@ -477,7 +510,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
     constexpr int CW = kPairThreads * VN;
     const int n = a.n;
     const int nchunks = (n + CW - 1) / CW;
-    const int cnt = *a.count;
+    const int cnt = *a.pcount;
     const int64_t W = a.wpre[cnt];
     const int npieces = gridDim.x * kPairPieces;
     int cur = -1, s = -1, U_ = 0;   // the row whose plan is staged
@@ -510,7 +543,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
                 if (a.wpre[i] + (int64_t)c * wc >= hi) break;
                 if (i != cur) {
                     cur = i;
-                    s = a.rows[i];
+                    s = a.prows[i];
                     U_ = (int)wc - 1;
                     __syncthreads();   // the previous row's plan is no longer read
                     if (threadIdx.x < U_) {
@@ -600,6 +633,8 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.plan = reinterpret_cast<PairTgt*>(d.plan);
     a.wpre = d.pair_w;
     a.next_piece = d.counts + 4;
+    a.prows = d.pair_rows;
+    a.pcount = d.counts + 5;
     a.tcap = d.tcap;
     a.rows = d.acc_rows;
     a.count = d.counts + 1;
@@ -618,7 +653,7 @@ void launch_pairdep(const Dev& d) {
                                    : (d.n % 2 == 0 ? 2 : 1);
     const int cw = kPairThreads * vn;
     k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
-                                          d.pair_w, d.stats, d.counts + 4, d.err);
+                                          d.pair_rows, d.counts + 5, d.pair_w, d.stats, d.counts + 4, d.err);
     const int grid = d.nsm * kPairCtasPerSm;   // one resident wave; later pieces go to the first free CTA
     if (d.dbytes == 4) {
         if (vn == 8) k_pairdep<int32_t, 8><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
