@@ -131,42 +131,69 @@ __device__ __forceinline__ void dev_alg4_out(int t, int n, const DT* __restrict_
 }
 
 // Stable compaction of {s : mark[s]} (or of all s when full) into rows[], one CTA.
-// Optionally clears mark[] and accumulates the per-update counters.
+// Optionally clears mark[] and accumulates the per-update counters.  A thread takes 16
+// consecutive flags per tile (one 16-byte load where aligned), so n = 16384 is one tile:
+// one block scan instead of one per 1024 flags.
 constexpr int kCompactThreads = 1024;
+constexpr int kCompactPerThread = 16;
 // Every thread of the block calls it; blockDim.x is a multiple of 32 (at most 1024).
 __device__ __forceinline__ void dev_compact(int n, uint8_t* mark, int clear, int32_t* rows, int32_t* count,
                                             int full, int64_t* stats, const int32_t* err) {
+    constexpr int E = kCompactPerThread;
     __shared__ int32_t wsum[32];
     __shared__ int32_t s_total;
     const int nwarps = blockDim.x >> 5;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool bad = *err != 0;
-    const unsigned lt = (1u << lane) - 1u;
     int base = 0;
-    for (int tile = 0; tile < n; tile += blockDim.x) {
-        const int s = tile + tid;
-        int f = 0;
-        if (s < n) {
-            f = (!bad && (full || mark[s] != 0)) ? 1 : 0;
-            if (clear) mark[s] = 0;
+    for (int tile = 0; tile < n; tile += (int)blockDim.x * E) {
+        const int s0 = tile + tid * E;
+        uint32_t fl = 0;   // bit e: flag of s0 + e
+        if (s0 < n) {
+            const bool vec = s0 + E <= n && ((reinterpret_cast<uintptr_t>(mark + s0) & 15) == 0);
+            if (vec) {
+                const uint4 v = *reinterpret_cast<const uint4*>(mark + s0);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((w[e >> 2] >> (8 * (e & 3))) & 0xFFu) fl |= 1u << e;
+                if (clear) *reinterpret_cast<uint4*>(mark + s0) = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                for (int e = 0; e < E && s0 + e < n; ++e) {
+                    if (mark[s0 + e]) fl |= 1u << e;
+                    if (clear) mark[s0 + e] = 0;
+                }
+            }
+            if (full) fl = (s0 + E <= n) ? 0xFFFFu : ((1u << (n - s0)) - 1u);
+            if (bad) fl = 0;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const int wpre = __popc(bal & lt);
-        if (lane == 0) wsum[wid] = __popc(bal);
+        const int c = __popc(fl);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
         __syncthreads();
         if (wid == 0) {
             const int x = lane < nwarps ? wsum[lane] : 0;
-            int incl = x;
+            int winc = x;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+                const int y = __shfl_up_sync(0xffffffffu, winc, o);
+                if (lane >= o) winc += y;
             }
-            if (lane < nwarps) wsum[lane] = incl - x;
-            if (lane == 31) s_total = incl;
+            if (lane < nwarps) wsum[lane] = winc - x;
+            if (lane == 31) s_total = winc;
         }
         __syncthreads();
-        if (f) rows[base + wsum[wid] + wpre] = s;
+        int pos = base + wsum[wid] + incl - c;
+        while (fl) {
+            const int e = __ffs(fl) - 1;
+            fl &= fl - 1;
+            rows[pos++] = s0 + e;
+        }
         base += s_total;
         __syncthreads();
     }
