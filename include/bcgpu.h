@@ -244,6 +244,14 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
  *                     for s.  Off: every changed source is re-accumulated (Section 5).
  *                     The two give the same D and sigma bit for bit and dependencies
  *                     within rounding.
+ *   "pair_walk" 0|1 (undirected graphs only; BC_ERR_ARG on a directed graph): find the
+ *                     columns of each changed pair (s,t) -- the vertices on a shortest
+ *                     s-t path of the old and of the new state -- by walking DAG(s) of
+ *                     Eq. 1 backwards from t over the E* superset, instead of testing
+ *                     every column.  Same results bit for bit.  Turning it on allocates
+ *                     its scratch (16 bytes per vertex per warp of the walk grid) once;
+ *                     BC_ERR_OOM if that fails, BC_ERR_ARG if n is too large for the
+ *                     walk's per-warp bit sets (n above ~100k).
  */
 int bc_set_option(bc_graph* g, const char* name, int64_t value);
 

@@ -409,12 +409,38 @@ void mirror_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, std::v
     }
 }
 
+// Scratch of the DAG walks (per warp of the walk grid: a vertex list, a touched-column
+// list and a row of column sums), allocated once per handle.
+int walk_alloc(bc_graph* g) {
+    Dev& d = g->d;
+    if (d.walk_list) return BC_OK;
+    if (walk_smem(d.n) > kWalkSmemMax) return fail(g, BC_ERR_ARG, "pair_walk: n too large for the walk's bit sets");
+    const size_t cells = (size_t)walk_warps(d.nsm) * (size_t)d.n;
+    int rc;
+    if ((rc = dalloc(g, &d.walk_list, cells)) || (rc = dalloc(g, &d.walk_touched, cells)) ||
+        (rc = dalloc(g, &d.walk_acc, cells)))
+        return rc;
+    return BC_OK;
+}
+
 int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const VEdge* d_ent) {
     Dev& d = g->d;
     std::vector<EOp> ops;
     std::vector<EMove> moves;
     std::vector<HArc> arcs;
     bool rebuild = false;
+    // the DAG walks of the pair corrections need the update's edges with their old weights
+    WalkUpd upd{};
+    const bool walk = d.pair_on && d.pair_walk && !g->directed && (int)ent.size() <= kWalkMaxEdges;
+    if (walk) {
+        upd.v = v;
+        upd.k = (int32_t)ent.size();
+        for (int j = 0; j < upd.k; ++j) {
+            upd.x[j] = ent[j].x;
+            auto it = g->wmap.find(arc_key(ent[j].x, v));
+            upd.wold[j] = it == g->wmap.end() ? -1 : it->second;
+        }
+    }
     mirror_update(g, v, ent, ops, moves, arcs, &rebuild);
     // moves made before a rebuild was found necessary are applied too: the rebuild reads
     // the device slots against the host mirror
@@ -478,11 +504,11 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
             CK(g, cudaStreamWaitEvent(g->side, g->ev_fork, 0));
             launch_accum_rows(ds, d.full_rows, d.counts + 3);
             CK(g, cudaEventRecord(g->ev_join, g->side));
-            launch_pairdep(d);
+            launch_pairdep(d, walk ? &upd : nullptr);
             CK(g, cudaStreamWaitEvent(d.st, g->ev_join, 0));
             g->launches += 4;
         } else {
-            timed(g, 5, 3, [&] { launch_pairdep(d); });
+            timed(g, 5, 3, [&] { launch_pairdep(d, walk ? &upd : nullptr); });
             timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
         }
         timed(g, 2, 3, [&] {
@@ -675,6 +701,11 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
                         std::string(#call) + ": " + cudaGetErrorString(e_));               \
     } while (0)
     CKI(scan_setup());
+    CKI(walk_setup());
+    if (!dir && n >= kWalkDefaultMinN) {
+        if ((rc = walk_alloc(g))) return bail(rc, g->last_error);
+        d.pair_walk = 1;
+    }
     CKI(cudaMemsetAsync(d.err, 0, sizeof(int32_t), d.st));
     CKI(cudaMemsetAsync(d.stats, 0, kStats * sizeof(int64_t), d.st));
     CKI(cudaMemsetAsync(d.mark, 0, n, d.st));
@@ -959,6 +990,15 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
     }
     if (std::strcmp(name, "profile") == 0) {
         g->profile = value != 0;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "pair_walk") == 0) {
+        if (value != 0 && g->directed) return fail(g, BC_ERR_ARG, "pair_walk needs an undirected graph");
+        if (value != 0) {
+            const int rc = walk_alloc(g);
+            if (rc) return rc;
+        }
+        g->d.pair_walk = value != 0 ? 1 : 0;
         return BC_OK;
     }
     if (std::strcmp(name, "pair_updates") == 0) {

@@ -82,6 +82,21 @@ template <> struct __align__(16) Arc<int64_t> { int64_t dst; int64_t w; };
 
 constexpr int kPairCap = 128;   // changed targets of a row corrected pair by pair (k_pair.cu)
 
+// The edges of one update as the DAG walks of the pair corrections need them: the
+// updated vertex v, the other endpoints x_j and the weight of {v, x_j} before the
+// update (-1: the edge is new).  Updates with more edges use the column test.
+constexpr int kWalkMaxEdges = 32;
+struct WalkUpd {
+    int32_t v;
+    int32_t k;
+    int32_t x[kWalkMaxEdges];
+    int64_t wold[kWalkMaxEdges];
+};
+constexpr int kWalkThreads = 256;
+constexpr int kWalkCtasPerSm = 4;
+constexpr size_t kWalkSmemMax = 200 * 1024;
+constexpr int kWalkDefaultMinN = 1 << 30;   // graphs with at least this many vertices walk by default
+
 // One edge of a vertex update, as staged on the device (matches bc_vedge).
 struct VEdge {
     int32_t x;
@@ -179,6 +194,10 @@ struct Dev {
     int64_t* pair_w;     // [n + 1] prefix of the pair corrections' work item weights
     int32_t* full_rows;  // [n] rows re-accumulated in full (counts[3])
     int32_t* pair_rows;  // [n] rows corrected pair by pair, most targets first (counts[5])
+    int32_t pair_walk;   // 1: pair corrections by DAG walks (k_pairwalk), scratch below allocated
+    int32_t* walk_list;      // [walk warps * n] per-warp vertex lists of the walks
+    int32_t* walk_touched;   // [walk warps * n] per-warp touched columns of a row
+    ff* walk_acc;            // [walk warps * n] per-warp column sums of a row (zero between rows)
     int64_t* bcfix;      // [2n] BC change of the corrected rows in this update, per column a
                          // fixed-point pair (units of 2^-24, units of 2^-56); zero between updates
     cudaStream_t st;
@@ -238,7 +257,10 @@ void launch_write_row(const Dev& d, int32_t v);
 void launch_estar_keep(const Dev& d, uint8_t* keep);
 PairRec pair_rec(const Dev& d);
 void launch_full_flags(const Dev& d);
-void launch_pairdep(const Dev& d);
+void launch_pairdep(const Dev& d, const WalkUpd* upd);   // upd: DAG walks (k_pairwalk), else column tests
+size_t walk_smem(int n);
+int64_t walk_warps(int nsm);
+cudaError_t walk_setup();
 void launch_pair_clear(const Dev& d);
 void launch_bc_fix(const Dev& d);
 

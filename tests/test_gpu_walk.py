@@ -1,0 +1,98 @@
+"""GPU parity of the DAG-walk form of the pair corrections (option "pair_walk") against
+the column-test form and the oracle.
+
+Both forms find the same columns (those on a shortest s-t path of each state) and sum
+the same terms in the same order (targets in plan order, old state first), so d, sigma,
+the dependency rows and BC must be bit-identical between them after every update; at
+the end of each stream both are compared with the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1311_2147_gb300 import binding, synth
+from tests.parity_util import compare_full
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    binding.load()
+
+
+def _walk_vs_test(g, ups, dist, label, every=1):
+    a = binding.BCGraph(g, dist=dist)
+    a.bc_set_option("pair_walk", 1)
+    b = binding.BCGraph(g, dist=dist)
+    b.bc_set_option("pair_walk", 0)
+    for i, up in enumerate(ups):
+        for h in (a, b):
+            rc, done = h.bc_apply_updates([up])
+            assert rc == 0 and done == 1, (label, up, h.last_error())
+        if (i + 1) % every and i + 1 != len(ups):
+            continue
+        da, sa, la = a.bc_get_rows()
+        db, sb, lb = b.bc_get_rows()
+        assert np.array_equal(da, db), f"{label}: distances differ after {up}"
+        assert np.array_equal(sa, sb), f"{label}: path counts differ after {up}"
+        bad = np.argwhere(la != lb)
+        assert bad.size == 0, f"{label}: dependencies differ after update {i} {up} at {bad[:5].tolist()}"
+        assert np.array_equal(a.bc_get_scores(), b.bc_get_scores()), f"{label}: BC differs after update {i}"
+    compare_full(a, synth.apply_updates(g, ups), label=label)
+    return a.bc_get_info()
+
+
+@pytest.mark.parametrize("dist", ["i32", "i64"])
+@pytest.mark.parametrize("wmax", [2, 9, 1000])
+def test_walk_matches_column_test_er(dist, wmax):
+    g = synth.erdos_renyi(80, 240, 1, wmax, 7000 + wmax, directed=False)
+    ups = synth.update_stream(g, 8, 8, 6, 7100 + wmax, 1, wmax, kmin=1, kmax=6)
+    info = _walk_vs_test(g, ups, dist, f"ER w<={wmax} {dist}")
+    assert info["pair_rows"] > 0
+
+
+def test_walk_matches_column_test_ba():
+    g, ups = synth.workload_ba16384(n=700, n_updates=30)
+    _walk_vs_test(g, ups, "i32", "BA n=700", every=5)
+
+
+def test_walk_ties_and_cycles():
+    # equal-length second routes: path counts grow, no distance drops
+    g = synth.cycle_graph(40, False, 1)
+    _walk_vs_test(g, [("edge", 0, 20, 20), ("edge", 10, 30, 20)], "i64", "cycle ties")
+
+
+def test_walk_joining_components_and_new_edges():
+    # new edges join components (their arcs did not exist in the old state)
+    a = synth.path_graph(12, False, 2)
+    k = 5
+    src = np.concatenate([a.src + 12 * i for i in range(k)]).astype(np.int32)
+    dst = np.concatenate([a.dst + 12 * i for i in range(k)]).astype(np.int32)
+    w = np.concatenate([a.w] * k).astype(np.int64)
+    g = synth.Graph(12 * k, False, src, dst, w)
+    ups = [("edge", 3, 15, 1), ("edge", 30, 50, 4), ("vertex", 40, [(2, 1, 0), (27, 3, 0)])]
+    _walk_vs_test(g, ups, "i32", "joining components")
+
+
+def test_walk_decrease_on_a_shortest_path():
+    # the lowered edge lay on old shortest paths: the old walks must use its old weight
+    g = synth.path_graph(50, False, 5)
+    ups = [("edge", 10, 11, 2), ("edge", 20, 21, 1), ("vertex", 30, [(29, 1, 0), (31, 2, 0), (5, 40, 0)])]
+    _walk_vs_test(g, ups, "i32", "decreases on path edges")
+
+
+def test_walk_long_stream():
+    g = synth.barabasi_albert(400, 3, 1, 30, 8181)
+    ups = synth.update_stream(g, 40, 40, 20, 8282, 1, 30, kmin=1, kmax=5)
+    _walk_vs_test(g, ups, "i32", "BA n=400, 100 updates", every=10)
+
+
+def test_walk_option_rejected_on_directed_graphs():
+    g = synth.erdos_renyi(20, 60, 1, 5, 3, directed=True)
+    a = binding.BCGraph(g)
+    with pytest.raises(binding.BCError) as e:
+        a.bc_set_option("pair_walk", 1)
+    assert e.value.code == binding.BC_ERR_ARG
