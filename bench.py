@@ -289,6 +289,7 @@ def run_ours(args):
     d_rows_acc, d_rows_scan = dinfo["rows_reaccumulated"], dinfo["rows_scanned"]
     d_low, d_tie = dinfo["pairs_lowered"], dinfo["pairs_tied"]
     d_full, d_pair_rows, d_pair_tgts = dinfo["rows_full"], dinfo["pair_rows"], dinfo["pair_targets"]
+    d_walk_pairs, d_walk_vtx, d_walk_arcs = dinfo["walk_pairs"], dinfo["walk_vertices"], dinfo["walk_arcs"]
     # algorithmic HBM bytes per kernel class over the profiled steps
     alg_bytes = {
         # rank-1 pass: read d of every scanned pair, sigma read+write on ties, d+sigma
@@ -307,10 +308,26 @@ def run_ours(args):
     alu_ops = {"pair_corrections": 4 * d_pair_tgts * n}
     peak, peak_kind = load_peaks()
     int_peak = int_alu_peak()
+    if d_walk_pairs:
+        # pair corrections by DAG walks: per E* arc examined the arc (8 B) and d(s,x) (sd B);
+        # per vertex found its segment bounds (8 B), two path counts (16 B), its list entry
+        # written and read back (8 B) and its buffer entry written and read (8 B)
+        alg_bytes["pair_corrections"] = d_walk_arcs * (8 + sd) + d_walk_vtx * (8 + 16 + 8 + 8)
+        alu_ops.pop("pair_corrections")
     dom = max(prof, key=lambda c: prof[c][0])
     dom_ms, dom_launches = prof[dom]
     roof = None
-    if dom in alu_ops and dom_ms > 0 and dom_launches > 0:
+    if dom == "pair_corrections" and d_walk_pairs and dom_ms > 0 and dom_launches > 0:
+        kl = len(prof_updates)
+        achieved = alg_bytes[dom] / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel_class": dom,
+                "kernel": "k_walk_units + k_walk_rows (DAG walks; with k_pair_plan, k_pair_weights)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes[dom] / kl,
+                "traffic": read_traffic("walks_ba8192", (d_walk_arcs + d_walk_vtx) / kl),
+                "launches": kl, "avg_launch_ms": dom_ms / kl,
+                "note": "latency-bound gathers along shortest-path DAGs; bytes counted per arc and vertex visited"}
+    elif dom in alu_ops and dom_ms > 0 and dom_launches > 0:
         kl = dom_launches // 3 or 1   # k_pair_plan, k_pair_weights, k_pairdep per update
         achieved = alu_ops[dom] / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel_class": dom, "kernel": "k_pairdep (with k_pair_plan, k_pair_weights)",
@@ -410,7 +427,8 @@ def run_ours(args):
     if rank == 0:
         rows_per_upd = (info1["rows_reaccumulated"] - info0["rows_reaccumulated"]) / len(timed)
         per_update = {k: (info1[k] - info0[k]) / len(timed)
-                      for k in ("rows_reaccumulated", "rows_full", "pair_rows", "pair_targets", "rows_scanned",
+                      for k in ("rows_reaccumulated", "rows_full", "pair_rows", "pair_targets", "walk_pairs",
+                                "walk_vertices", "walk_arcs", "rows_scanned",
                                 "pairs_lowered", "pairs_tied", "estar_moves", "estar_rebuilds")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -573,8 +591,9 @@ def run_ncu_case(args):
     """A small case of one kernel class for ncu captures (a few GB on the device at most):
     BA n=8192 (state 2.1 GB, above L2), static init, then either two vertex updates with
     every changed row re-accumulated (accumulation and BC rows), the first four updates
-    of the stream with pair corrections (pair), or two edge updates with the rank-1
-    pass over every row (the paper's all-pairs Step 2)."""
+    of the stream with pair corrections by the column test (pair) or by DAG walks
+    (walk), or two edge updates with the rank-1 pass over every row (the paper's
+    all-pairs Step 2)."""
     from paper_1311_2147_gb300 import binding, synth
     binding.load()
     g, ups = synth.workload_ba16384(n=args.ncu_n, n_updates=64)
@@ -583,6 +602,10 @@ def run_ncu_case(args):
         bg.bc_set_option("full_scan", 1)
         sel = [u for u in ups if u[0] == "edge"][:2]
     elif args.ncu_case == "pair":
+        bg.bc_set_option("pair_walk", 0)
+        sel = ups[:4]
+    elif args.ncu_case == "walk":
+        bg.bc_set_option("pair_walk", 1)
         sel = ups[:4]
     else:
         bg.bc_set_option("pair_updates", 0)
@@ -594,7 +617,8 @@ def run_ncu_case(args):
         assert rc == 0, bg.last_error()
         after = bg.bc_get_info()
         per_update.append({k: after[k] - before[k] for k in ("rows_reaccumulated", "rows_full", "pair_rows",
-                                                             "pair_targets", "rows_scanned", "pairs_lowered",
+                                                             "pair_targets", "walk_pairs", "walk_vertices",
+                                                             "walk_arcs", "rows_scanned", "pairs_lowered",
                                                              "pairs_tied")})
     print(json.dumps({"ncu_case": args.ncu_case, "n": g.n, "per_update": per_update, "info": bg.bc_get_info()}))
     return 0
@@ -617,7 +641,7 @@ def main():
     ap.add_argument("--recompute-runs", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
-    ap.add_argument("--ncu-case", choices=["accumulate", "pair", "scan"], default=None,
+    ap.add_argument("--ncu-case", choices=["accumulate", "pair", "walk", "scan"], default=None,
                     help="run only a small case of one kernel class (for ncu captures)")
     ap.add_argument("--ncu-n", type=int, default=8192)
     args = ap.parse_args()

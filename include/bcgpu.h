@@ -119,6 +119,10 @@ typedef struct bc_info {
     int64_t estar_moves;         /* vertex segments of E* moved to the free region instead */
     int64_t pair_rows;           /* rows whose dependencies were corrected pair by pair */
     int64_t pair_targets;        /* (row, changed target) pairs of those corrections */
+    int64_t walk_pairs;          /* of pair_targets: pairs whose columns were found by DAG walks
+                                    ("pair_walk") */
+    int64_t walk_vertices;       /* vertices on their shortest paths (both states) found by the walks */
+    int64_t walk_arcs;           /* E* superset arcs the walks examined */
 } bc_info;
 
 /*

@@ -57,7 +57,10 @@ class bc_info(ctypes.Structure):
                 ("state_bytes", ctypes.c_int64), ("last_init_ms", ctypes.c_double),
                 ("rows_full", ctypes.c_int64), ("estar_rebuilds", ctypes.c_int64),
                 ("estar_moves", ctypes.c_int64), ("pair_rows", ctypes.c_int64),
-                ("pair_targets", ctypes.c_int64)]
+                ("pair_targets", ctypes.c_int64),
+                ("walk_pairs", ctypes.c_int64),
+                ("walk_vertices", ctypes.c_int64),
+                ("walk_arcs", ctypes.c_int64)]
 
 
 RESULT_DTYPE = np.dtype([("request_id", "<i8"), ("graph_id", "<i4"), ("status", "<i4"),

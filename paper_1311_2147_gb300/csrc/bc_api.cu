@@ -70,6 +70,7 @@ struct bc_graph {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t bytes = 0;
     double last_init_ms = 0.0;
+    int64_t walk_cap_alloc = 0;   // entries allocated for the DAG walks' buffer
     std::vector<void*> allocs;
     // launch accounting and optional per-class event timing
     int64_t launches = 0;
@@ -415,11 +416,19 @@ int walk_alloc(bc_graph* g) {
     Dev& d = g->d;
     if (d.walk_list) return BC_OK;
     if (walk_smem(d.n) > kWalkSmemMax) return fail(g, BC_ERR_ARG, "pair_walk: n too large for the walk's bit sets");
-    const size_t cells = (size_t)walk_warps(d.nsm) * (size_t)d.n;
+    const size_t n = (size_t)d.n;
+    // expected use is ~25 entries per changed pair; every warp may leave part of a block unused
+    d.walk_cap = (int64_t)(8u << 20) + 64 * (int64_t)n + walk_warps(d.nsm) * kWalkBlock;
+    g->walk_cap_alloc = d.walk_cap;
     int rc;
-    if ((rc = dalloc(g, &d.walk_list, cells)) || (rc = dalloc(g, &d.walk_touched, cells)) ||
-        (rc = dalloc(g, &d.walk_acc, cells)))
+    if ((rc = dalloc(g, &d.walk_list, (size_t)walk_warps(d.nsm) * n)) ||
+        (rc = dalloc(g, &d.walk_buf, (size_t)d.walk_cap)) || (rc = dalloc(g, &d.walk_useg, n * kPairCap * 4)) ||
+        (rc = dalloc(g, &d.walk_acc2, (size_t)walk_ctas(d.nsm) * 2 * n)) ||
+        (rc = dalloc(g, &d.walk_tl, (size_t)walk_ctas(d.nsm) * n)) || (rc = dalloc(g, &d.walk_ctl, 8)))
         return rc;
+    cudaError_t e = cudaMemsetAsync(d.walk_acc2, 0, sizeof(int64_t) * (size_t)walk_ctas(d.nsm) * 2 * n, d.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.walk_ctl, 0, sizeof(int32_t) * 8, d.st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
     return BC_OK;
 }
 
@@ -974,6 +983,9 @@ int bc_get_info(bc_graph* g, bc_info* out) {
     out->rows_full = g->h_stats[7];
     out->pair_rows = g->h_stats[8];
     out->pair_targets = g->h_stats[9];
+    out->walk_pairs = g->h_stats[10];
+    out->walk_vertices = g->h_stats[11];
+    out->walk_arcs = g->h_stats[12];
     out->estar_rebuilds = g->estar_rebuilds;
     out->estar_moves = g->estar_moves;
     out->kernel_launches = g->launches;
@@ -999,6 +1011,14 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
             if (rc) return rc;
         }
         g->d.pair_walk = value != 0 ? 1 : 0;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "walk_cap") == 0) {
+        // entries of the walks' buffer to use (at most the allocated size; a test knob:
+        // an update whose walks do not fit is done by the column test)
+        if (!g->d.walk_list) return fail(g, BC_ERR_ARG, "walk_cap needs pair_walk on");
+        if (value < 0 || value > g->walk_cap_alloc) return fail(g, BC_ERR_ARG, "walk_cap out of range");
+        g->d.walk_cap = value;
         return BC_OK;
     }
     if (std::strcmp(name, "pair_updates") == 0) {

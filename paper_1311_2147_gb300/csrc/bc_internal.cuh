@@ -29,8 +29,9 @@ enum : int32_t { ERRF_OVERFLOW = 1, ERRF_DIST = 2, ERRF_TIMEOUT = 4, ERRF_ARG_DE
 // Per-handle device counters: [0] rows re-accumulated [1] no-op updates [2] most rows of
 // one update [3] updates [4] pairs lowered [5] pairs with new tied paths [6] rows scanned
 // [7] rows re-accumulated in full [8] rows corrected pair by pair [9] (row, target) pairs
-// of those corrections.
-constexpr int kStats = 10;
+// of those corrections [10] pairs corrected by DAG walks [11] vertices those walks found
+// [12] E* arcs they examined.
+constexpr int kStats = 13;
 
 // Saturation marker for a distance sum that does not fit: INT64_MAX.  For DT =
 // int64 this equals INF, so callers test for it before comparing.
@@ -93,9 +94,11 @@ struct WalkUpd {
     int64_t wold[kWalkMaxEdges];
 };
 constexpr int kWalkThreads = 256;
-constexpr int kWalkCtasPerSm = 4;
+constexpr int kWalkCtasPerSm = 8;      // walks: latency-bound, 32 registers, a few KB of shared memory
+constexpr int kWalkRowCtasPerSm = 8;
 constexpr size_t kWalkSmemMax = 200 * 1024;
-constexpr int kWalkDefaultMinN = 1 << 30;   // graphs with at least this many vertices walk by default
+constexpr int kWalkBlock = 2048;     // walk buffer entries a warp reserves at a time
+constexpr int kWalkDefaultMinN = 12288;   // undirected graphs with at least this many vertices walk by default
 
 // One edge of a vertex update, as staged on the device (matches bc_vedge).
 struct VEdge {
@@ -194,10 +197,14 @@ struct Dev {
     int64_t* pair_w;     // [n + 1] prefix of the pair corrections' work item weights
     int32_t* full_rows;  // [n] rows re-accumulated in full (counts[3])
     int32_t* pair_rows;  // [n] rows corrected pair by pair, most targets first (counts[5])
-    int32_t pair_walk;   // 1: pair corrections by DAG walks (k_pairwalk), scratch below allocated
-    int32_t* walk_list;      // [walk warps * n] per-warp vertex lists of the walks
-    int32_t* walk_touched;   // [walk warps * n] per-warp touched columns of a row
-    ff* walk_acc;            // [walk warps * n] per-warp column sums of a row (zero between rows)
+    int32_t pair_walk;   // 1: pair corrections by DAG walks (k_walk_units, k_walk_rows), scratch below
+    int32_t* walk_list;      // [walk warps * n] per-warp vertex lists of a walk
+    int32_t* walk_buf;       // [walk_cap] vertices found by the walks of an update
+    int64_t walk_cap;
+    int32_t* walk_useg;      // [n * tcap * 4] per (row, target): segments of the old and new walk
+    int64_t* walk_acc2;      // [walk CTAs * 2n] per-CTA fixed-point column sums of a row (zero between rows)
+    int32_t* walk_tl;        // [walk CTAs * n] per-CTA touched columns of a row
+    int32_t* walk_ctl;       // [8] units and rows handed out, buffer used (64-bit), overflow
     int64_t* bcfix;      // [2n] BC change of the corrected rows in this update, per column a
                          // fixed-point pair (units of 2^-24, units of 2^-56); zero between updates
     cudaStream_t st;
@@ -260,6 +267,7 @@ void launch_full_flags(const Dev& d);
 void launch_pairdep(const Dev& d, const WalkUpd* upd);   // upd: DAG walks (k_pairwalk), else column tests
 size_t walk_smem(int n);
 int64_t walk_warps(int nsm);
+int64_t walk_ctas(int nsm);
 cudaError_t walk_setup();
 void launch_pair_clear(const Dev& d);
 void launch_bc_fix(const Dev& d);

@@ -84,6 +84,7 @@ struct PairArgs {
     int32_t* next_piece;    // pieces of the work handed out so far past the first wave
     const int32_t* prows;   // the rows corrected pair by pair, most targets first
     const int32_t* pcount;
+    const int32_t* gate;    // when set: the column test runs only if *gate != 0 (walk overflow)
     int tcap;
     const int32_t* rows;
     const int32_t* count;
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
                                                        const int32_t* tcnt, int tcap, int nchunks,
                                                        int32_t* prows, int32_t* pcount,
                                                        int64_t* wpre, int64_t* stats, int32_t* next_piece,
-                                                       const int32_t* err) {
+                                                       int32_t* walk_ctl, const int32_t* err) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total;
     __shared__ int64_t s_rows[32], s_tgts[32];
@@ -330,6 +331,8 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
         }
         wpre[cnt] = base;
         *next_piece = 0;
+        if (walk_ctl)
+            for (int k = 0; k < 8; ++k) walk_ctl[k] = 0;
         stats[8] += r;
         stats[9] += t;
     }
@@ -507,6 +510,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
     __shared__ PairQueue s_wq[kPairThreads / 32];
     __shared__ int s_i, s_c, s_p;
     if (*a.err) return;
+    if (a.gate && *a.gate == 0) return;
     constexpr int CW = kPairThreads * VN;
     const int n = a.n;
     const int nchunks = (n + CW - 1) / CW;
@@ -635,6 +639,7 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.next_piece = d.counts + 4;
     a.prows = d.pair_rows;
     a.pcount = d.counts + 5;
+    a.gate = nullptr;
     a.tcap = d.tcap;
     a.rows = d.acc_rows;
     a.count = d.counts + 1;
@@ -646,33 +651,44 @@ static PairArgs<DT> pair_args(const Dev& d) {
 
 // ------------------------------------------------------------------ DAG walks
 //
-// The same corrections found by walking the shortest-path DAG instead of testing every
-// column.  The columns on a shortest s-t path of a state are the vertices from which t
-// is reachable in DAG(s) of that state (Eq. 1: the arcs (x, y) with d(s,x) + w(x,y) =
-// d(s,y)), so a walk backwards from t over those arcs visits exactly them -- about 20
-// per changed pair against n column tests.  In G_D of an undirected graph the arcs into
-// y are y's own arcs reversed (same weight), read from the E* superset; before the
-// update E*+ held every arc of the old E* (arcs are only added between re-layouts, and
-// a re-layout keeps the arcs of the state it reads), and the arcs of the update itself
-// carry their old weight from `upd` (or did not exist).  One warp takes a row (the
-// rows go out most targets first), walks its targets in plan order, old state first,
-// level by level (the arcs of a level's vertices spread over the lanes), and sums the
-// terms of each column in a per-warp scratch row in that order -- the same order, and
-// so the same sums, as k_pairdep -- before adding them to delta_s and BC once.
+// The same corrections with the columns found by walking the shortest-path DAG instead
+// of testing every column.  The columns on a shortest s-t path of a state are the
+// vertices from which t is reachable in DAG(s) of that state (Eq. 1: the arcs (x, y)
+// with d(s,x) + w(x,y) = d(s,y)), so a walk backwards from t over those arcs visits
+// exactly them -- about 20 per changed pair against n column tests.  In G_D of an
+// undirected graph the arcs into y are y's own arcs reversed (same weight), read from
+// the E* superset; before the update E*+ held every arc of the old E* (arcs are only
+// added between re-layouts, and a re-layout keeps the arcs of the state it reads), and
+// the arcs of the update itself carry their old weight from `upd` (or did not exist).
+//
+// Phase 1 (k_walk_units): a unit is one changed pair (row s, target); any free warp
+// takes the next units, walks both states level by level (the arcs of a level's
+// vertices spread over the lanes) and appends the vertices found -- t excluded -- to a
+// global buffer, recording each walk's segment.  Phase 2 (k_walk_rows): one CTA per row;
+// its warps share out the row's segments, evaluate the terms and add them to a per-CTA
+// row of fixed-point column sums (integer atomics, so the sums do not depend on which
+// warp adds first), which is then added to delta_s and to BC's fixed-point change.  If
+// the buffer overflows, phase 2 does nothing and the column test runs instead.
 
 template <typename DT>
 struct WalkArgs {
     const int32_t* e_off;
     const int32_t* e_len;
     const Arc<DT>* e_arc;
-    int32_t* list;      // [warps * n] vertices of the current walk, level by level
-    int32_t* touched;   // [warps * n] columns with a sum in acc
-    ff* acc;            // [warps * n] column sums of the current row
-    int32_t* next_row;  // rows handed out so far
+    int32_t* list;      // [walk warps * n] vertices of a walk, level by level (phase 1)
+    int32_t* buf;       // [cap] vertices found by the walks of the update's units
+    int64_t cap;
+    int32_t* useg;      // [n * tcap * 4] per unit: start and length of the old, then the new walk
+    int64_t* acc2;      // [CTAs * 2n] per CTA: fixed-point column sums of a row (zero between rows)
+    int32_t* tl;        // [CTAs * n] per CTA: columns of the row with a sum
+    int32_t* ctl;       // [0] units handed out [1] rows handed out [2..3] buffer used (64-bit) [4] overflow
+    int64_t* stats;     // [10] pairs walked [11] vertices found [12] arcs examined
+    int nchunks;        // items per row in the weight prefix wpre
     WalkUpd upd;
 };
 
 constexpr int kWalkWarps = kWalkThreads / 32;
+constexpr int kWalkGrab = 4;         // units a warp takes at a time
 
 // d(s,x) of a state: the saved value where the pair changed in this update (old state).
 template <typename DT>
@@ -688,150 +704,266 @@ __device__ __forceinline__ uint64_t walk_sigma(const PairArgs<DT>& a, size_t rs,
     return a.S[i];
 }
 
+// First unit of row index r: the targets of the rows before it (wpre counts T + 1 per
+// row and item chunk).
 template <typename DT>
-__global__ void __launch_bounds__(kWalkThreads) k_pairwalk(PairArgs<DT> a, WalkArgs<DT> w) {
-    extern __shared__ uint32_t wbits[];   // per warp: visited bits, then touched bits
+__device__ __forceinline__ int64_t unit_start(const PairArgs<DT>& a, int nchunks, int r) {
+    return a.wpre[r] / nchunks - r;
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(PairArgs<DT> a, WalkArgs<DT> w) {
+    extern __shared__ uint32_t wbits[];   // per warp: visited bits
     if (*a.err) return;
     const int n = a.n, words = a.words;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t INF = Inf<DT>::v;
-    uint32_t* vis = wbits + (size_t)wib * 2 * words;
-    uint32_t* tch = vis + words;
-    const size_t gw = (size_t)blockIdx.x * kWalkWarps + wib;
-    int32_t* list = w.list + gw * n;
-    int32_t* tlist = w.touched + gw * n;
-    ff* acc = w.acc + gw * n;
-    for (int i = lane; i < 2 * words; i += 32) vis[i] = 0u;
+    uint32_t* vis = wbits + (size_t)wib * words;
+    int32_t* list = w.list + ((size_t)blockIdx.x * kWalkWarps + wib) * n;
+    for (int i = lane; i < words; i += 32) vis[i] = 0u;
     __syncwarp();
     const int cnt = *a.pcount;
+    const int64_t nunits = unit_start<DT>(a, w.nchunks, cnt);
     const int v = w.upd.v;
+    // this warp's block of the buffer: [bnext, bend)
+    long long bnext = 0, bend = 0;
+    long long n_found = 0, n_arcs = 0;   // counters (lane 0 adds them to stats at the end)
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 10), (unsigned long long)nunits);
     for (;;) {
-        int r = 0;
-        if (lane == 0) r = atomicAdd(w.next_row, 1);
-        r = __shfl_sync(0xffffffffu, r, 0);
-        if (r >= cnt) break;
-        const int s = a.prows[r];
-        const int T = a.tcnt[s];
-        const PairTgt* pl = a.plan + (size_t)s * a.tcap;
-        const size_t rs = (size_t)s * n;
-        int ntouch = 0;   // warp-uniform
-        for (int u = 0; u < T; ++u) {
-            const int t = pl[u].t;
-            const size_t rt = (size_t)t * n;
+        int g0 = 0;
+        if (lane == 0) g0 = atomicAdd(w.ctl, kWalkGrab);
+        g0 = __shfl_sync(0xffffffffu, g0, 0);
+        if (g0 >= nunits) break;
+        for (int64_t id = g0; id < min((int64_t)g0 + kWalkGrab, nunits); ++id) {
+            // the unit's row: the last r with unit_start(r) <= id
+            int L = 0, R = cnt;
+            while (R - L > 1) {
+                const int m = (L + R) >> 1;
+                if (unit_start<DT>(a, w.nchunks, m) <= id) L = m; else R = m;
+            }
+            const int s = a.prows[L];
+            const int u = (int)(id - unit_start<DT>(a, w.nchunks, L));
+            const PairTgt& pt = a.plan[(size_t)s * a.tcap + u];
+            const int t = pt.t;
+            const size_t rs = (size_t)s * n;
             for (int stt = 0; stt < 2; ++stt) {
                 const bool is_new = stt == 1;
-                if ((is_new ? pl[u].dnew : pl[u].dold) < 0) continue;   // no path in this state
-                const ff rcp = is_new ? pl[u].rnew : pl[u].rold;
-                if (lane == 0) {
-                    list[0] = t;
-                    vis[t >> 5] |= 1u << (t & 31);
-                }
-                __syncwarp();
-                int head = 0, tail = 1;   // warp-uniform; list[head, tail) is the current level
-                while (head < tail) {
-                    const int l0 = head, l1 = tail;
-                    head = l1;
-                    for (int b0 = l0; b0 < l1; b0 += 32) {
-                        const int nb = min(32, l1 - b0);
-                        int y = 0, off = 0, len = 0;
-                        int64_t dy = 0;
-                        if (lane < nb) {
-                            y = list[b0 + lane];
-                            off = w.e_off[y];
-                            len = w.e_len[y];
-                            dy = walk_d<DT>(a, rs, s, y, is_new);
-                        }
-                        int incl = len;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int z = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += z;
-                        }
-                        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                        const int excl = incl - len;
-                        for (int k0 = 0; k0 < tot; k0 += 32) {   // the batch's arcs, one per lane
-                            const int k = k0 + lane;
-                            // owner: the last lane j < nb whose arcs start at or before k
-                            int j = 0;
-#pragma unroll
-                            for (int step = 16; step >= 1; step >>= 1) {
-                                const int c = j + step;
-                                const int ex = __shfl_sync(0xffffffffu, excl, c & 31);
-                                if (c < nb && ex <= k) j = c;
-                            }
-                            const int yj = __shfl_sync(0xffffffffu, y, j);
-                            const int offj = __shfl_sync(0xffffffffu, off, j);
-                            const int exj = __shfl_sync(0xffffffffu, excl, j);
-                            const int64_t dyj = __shfl_sync(0xffffffffu, dy, j);
-                            bool fresh = false;
-                            int x = -1;
-                            if (k < tot) {
-                                const Arc<DT> arc = w.e_arc[offj + (k - exj)];
-                                x = (int)arc.dst;
-                                int64_t wv = (int64_t)arc.w;
-                                if (!is_new && (yj == v || x == v)) {
-                                    const int o = yj == v ? x : yj;
-                                    for (int e = 0; e < w.upd.k; ++e)
-                                        if (w.upd.x[e] == o) wv = w.upd.wold[e];
-                                }
-                                if (x >= 0 && x != s && wv >= 0) {
-                                    const int64_t dx = walk_d<DT>(a, rs, s, x, is_new);
-                                    if (dx != INF && dx + wv == dyj) {
-                                        const uint32_t bit = 1u << (x & 31);
-                                        fresh = !(atomicOr(&vis[x >> 5], bit) & bit);
-                                    }
-                                }
-                            }
-                            const unsigned bal = __ballot_sync(0xffffffffu, fresh);
-                            bool first = false;
-                            if (fresh) {
-                                list[tail + __popc(bal & lt)] = x;
-                                // the pair term of column x, added to its sum in walk order (a
-                                // column occurs once per walk)
-                                ff term = pair_term(walk_sigma<DT>(a, rs, s, x, is_new),
-                                                    walk_sigma<DT>(a, rt, t, x, is_new), rcp);
-                                if (!is_new) term = ff{-term.hi, -term.lo};
-                                const uint32_t bit = 1u << (x & 31);
-                                first = !(atomicOr(&tch[x >> 5], bit) & bit);
-                                acc[x] = ff_add(first ? ff{0.f, 0.f} : acc[x], term);
-                            }
-                            const unsigned bf = __ballot_sync(0xffffffffu, first);
-                            if (first) tlist[ntouch + __popc(bf & lt)] = x;
-                            ntouch += __popc(bf);
-                            tail += __popc(bal);
-                        }
+                int found = 0;   // warp-uniform
+                if ((is_new ? pt.dnew : pt.dold) >= 0) {
+                    if (lane == 0) {
+                        list[0] = t;
+                        vis[t >> 5] |= 1u << (t & 31);
                     }
                     __syncwarp();
+                    int head = 0, tail = 1;   // list[head, tail) is the current level
+                    while (head < tail) {
+                        const int l0 = head, l1 = tail;
+                        head = l1;
+                        for (int b0 = l0; b0 < l1; b0 += 32) {
+                            const int nb = min(32, l1 - b0);
+                            int y = 0, off = 0, len = 0;
+                            int64_t dy = 0;
+                            if (lane < nb) {
+                                y = list[b0 + lane];
+                                off = w.e_off[y];
+                                len = w.e_len[y];
+                                dy = walk_d<DT>(a, rs, s, y, is_new);
+                            }
+                            int incl = len;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int z = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += z;
+                            }
+                            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                            const int excl = incl - len;
+                            n_arcs += tot;
+                            for (int k0 = 0; k0 < tot; k0 += 32) {   // the batch's arcs, one per lane
+                                const int k = k0 + lane;
+                                int j = 0;   // owner: the last lane j < nb whose arcs start at or before k
+#pragma unroll
+                                for (int step = 16; step >= 1; step >>= 1) {
+                                    const int c = j + step;
+                                    const int ex = __shfl_sync(0xffffffffu, excl, c & 31);
+                                    if (c < nb && ex <= k) j = c;
+                                }
+                                const int yj = __shfl_sync(0xffffffffu, y, j);
+                                const int offj = __shfl_sync(0xffffffffu, off, j);
+                                const int exj = __shfl_sync(0xffffffffu, excl, j);
+                                const int64_t dyj = __shfl_sync(0xffffffffu, dy, j);
+                                bool fresh = false;
+                                int x = -1;
+                                if (k < tot) {
+                                    const Arc<DT> arc = w.e_arc[offj + (k - exj)];
+                                    x = (int)arc.dst;
+                                    int64_t wv = (int64_t)arc.w;
+                                    if (!is_new && (yj == v || x == v)) {
+                                        const int o = yj == v ? x : yj;
+                                        for (int e = 0; e < w.upd.k; ++e)
+                                            if (w.upd.x[e] == o) wv = w.upd.wold[e];
+                                    }
+                                    if (x >= 0 && x != s && wv >= 0) {
+                                        const int64_t dx = walk_d<DT>(a, rs, s, x, is_new);
+                                        if (dx != INF && dx + wv == dyj) {
+                                            const uint32_t bit = 1u << (x & 31);
+                                            fresh = !(atomicOr(&vis[x >> 5], bit) & bit);
+                                        }
+                                    }
+                                }
+                                const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+                                if (fresh) list[tail + __popc(bal & lt)] = x;
+                                tail += __popc(bal);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    found = tail - 1;
+                    n_found += found;
+                    // the walk's vertices (t excluded) into the buffer
+                    // room in the warp's block, else a new block (a walk longer than a block
+                    // gets a block of its own size); one atomic per block, not per walk
+                    if (bnext + found > bend) {
+                        const long long want = found > kWalkBlock ? found : kWalkBlock;
+                        long long b = 0;
+                        if (lane == 0)
+                            b = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(w.ctl + 2),
+                                                     (unsigned long long)want);
+                        bnext = __shfl_sync(0xffffffffu, b, 0);
+                        bend = bnext + want;
+                    }
+                    const long long base = bnext;
+                    bnext += found;
+                    if (base + found <= w.cap) {
+                        for (int i = lane; i < found; i += 32) w.buf[base + i] = list[1 + i];
+                    } else {
+                        if (lane == 0) w.ctl[4] = 1;
+                        found = 0;
+                    }
+                    if (lane == 0) w.useg[id * 4 + 2 * stt] = (int32_t)base;
+                    for (int i = lane; i < tail; i += 32) vis[list[i] >> 5] = 0u;
+                    __syncwarp();
                 }
-                // clear the visited bits of this walk
-                for (int i = lane; i < tail; i += 32) vis[list[i] >> 5] = 0u;
-                __syncwarp();
+                if (lane == 0) w.useg[id * 4 + 2 * stt + 1] = found;
             }
         }
-        // the row's sums: delta_s and BC once per column
-        for (int i = lane; i < ntouch; i += 32) {
-            const int x = tlist[i];
-            const ff sum = acc[x];
-            ff* p = a.Dl + rs + x;
-            *p = ff_add(*p, sum);
-            bc_fix_add(a.bcfix, x, sum);
-            tch[x >> 5] = 0u;
-        }
-        __syncwarp();
+    }
+    if (lane == 0 && (n_found | n_arcs)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 11), (unsigned long long)n_found);
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 12), (unsigned long long)n_arcs);
     }
 }
 
-size_t walk_smem(int n) { return (size_t)kWalkWarps * 2 * (size_t)((n + 31) / 32) * sizeof(uint32_t); }
+// A term as a fixed-point pair (units of 2^-24, 2^-56), as in bc_fix_add.
+__device__ __forceinline__ void fix_split(ff v, long long* A, long long* B) {
+    const double vd = ((double)v.hi + (double)v.lo) * 0x1p24;
+    const double a = rint(vd);
+    *A = (long long)a;
+    *B = __double2ll_rn((vd - a) * 0x1p32);
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(PairArgs<DT> a, WalkArgs<DT> w) {
+    extern __shared__ uint32_t tbits[];   // touched columns of the row
+    __shared__ int s_r, s_nt;
+    if (*a.err) return;
+    if (*(volatile int32_t*)(w.ctl + 4)) return;   // overflow: the column test does the update
+    const int n = a.n, words = a.words;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    long long* acc = reinterpret_cast<long long*>(w.acc2) + (size_t)blockIdx.x * 2 * n;
+    int32_t* tl = w.tl + (size_t)blockIdx.x * n;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) tbits[i] = 0u;
+    const int cnt = *a.pcount;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_r = atomicAdd(w.ctl + 1, 1);
+            s_nt = 0;
+        }
+        __syncthreads();
+        const int r = s_r;
+        if (r >= cnt) break;
+        const int s = a.prows[r];
+        const int T = a.tcnt[s];
+        const int64_t id0 = unit_start<DT>(a, w.nchunks, r);
+        const size_t rs = (size_t)s * n;
+        // the row's walks (2 per target) go to the warps in turn
+        for (int q = wib; q < 2 * T; q += kWalkWarps) {
+            const int u = q >> 1;
+            const bool is_new = q & 1;
+            const PairTgt& pt = a.plan[(size_t)s * a.tcap + u];
+            const int64_t base = w.useg[(id0 + u) * 4 + 2 * (q & 1)];
+            const int len = w.useg[(id0 + u) * 4 + 2 * (q & 1) + 1];
+            const ff rcp = is_new ? pt.rnew : pt.rold;
+            const size_t rt = (size_t)pt.t * n;
+            for (int i = lane; i < len; i += 32) {
+                const int x = w.buf[base + i];
+                ff term = pair_term(walk_sigma<DT>(a, rs, s, x, is_new), walk_sigma<DT>(a, rt, pt.t, x, is_new), rcp);
+                if (!is_new) term = ff{-term.hi, -term.lo};
+                long long A, B;
+                fix_split(term, &A, &B);
+                atomicAdd(reinterpret_cast<unsigned long long*>(acc + 2 * x), (unsigned long long)A);
+                if (B) atomicAdd(reinterpret_cast<unsigned long long*>(acc + 2 * x + 1), (unsigned long long)B);
+                const uint32_t bit = 1u << (x & 31);
+                if (!(atomicOr(&tbits[x >> 5], bit) & bit)) tl[atomicAdd(&s_nt, 1)] = x;
+            }
+        }
+        __syncthreads();
+        // the row's sums: delta_s and BC's change once per column, then the scratch back to zero
+        const int nt = s_nt;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int x = tl[i];
+            const long long A0 = acc[2 * x], B0 = acc[2 * x + 1];
+            acc[2 * x] = 0;
+            acc[2 * x + 1] = 0;
+            const long long A = A0 + (B0 >> 32), B = B0 & 0xFFFFFFFFll;
+            const double hi = (double)A * 0x1p-24, lo = (double)B * 0x1p-56;
+            const double sum = hi + lo;
+            const float f1 = (float)sum;
+            const ff v{f1, (float)((sum - (double)f1) + ((hi - sum) + lo))};
+            ff* p = a.Dl + rs + x;
+            *p = ff_add(*p, v);
+            unsigned long long* bp = reinterpret_cast<unsigned long long*>(a.bcfix + 2 * (size_t)x);
+            atomicAdd(bp, (unsigned long long)A0);
+            if (B0) atomicAdd(bp + 1, (unsigned long long)B0);
+            tbits[x >> 5] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+size_t walk_smem(int n) { return (size_t)kWalkWarps * (size_t)((n + 31) / 32) * sizeof(uint32_t); }
 int64_t walk_warps(int nsm) { return (int64_t)nsm * kWalkCtasPerSm * kWalkWarps; }
+int64_t walk_ctas(int nsm) { return (int64_t)nsm * kWalkRowCtasPerSm; }
 
 cudaError_t walk_setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_pairwalk<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_walk_units<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kWalkSmemMax);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pairwalk<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_walk_units<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kWalkSmemMax);
     return e;
+}
+
+template <typename DT>
+static void launch_walks(const Dev& d, const WalkUpd& upd, int nchunks, int vn) {
+    const int grid = d.nsm * kWalkCtasPerSm, rgrid = d.nsm * kWalkRowCtasPerSm;
+    WalkArgs<DT> w{d.e_off, d.e_len, (const Arc<DT>*)d.e_arc, d.walk_list, d.walk_buf, d.walk_cap, d.walk_useg,
+                   d.walk_acc2, d.walk_tl, d.walk_ctl, d.stats, nchunks, upd};
+    k_walk_units<DT><<<grid, kWalkThreads, walk_smem(d.n), d.st>>>(pair_args<DT>(d), w);
+    k_walk_rows<DT><<<rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), d.st>>>(pair_args<DT>(d), w);
+    // the column test, which does nothing unless the walks' buffer overflowed
+    PairArgs<DT> a = pair_args<DT>(d);
+    a.gate = d.walk_ctl + 4;
+    const int pgrid = d.nsm * kPairCtasPerSm;
+    if constexpr (sizeof(DT) == 4) {
+        if (vn == 8) k_pairdep<DT, 8><<<pgrid, kPairThreads, 0, d.st>>>(a);
+        else if (vn == 4) k_pairdep<DT, 4><<<pgrid, kPairThreads, 0, d.st>>>(a);
+        else k_pairdep<DT, 1><<<pgrid, kPairThreads, 0, d.st>>>(a);
+    } else {
+        if (vn == 2) k_pairdep<DT, 2><<<pgrid, kPairThreads, 0, d.st>>>(a);
+        else k_pairdep<DT, 1><<<pgrid, kPairThreads, 0, d.st>>>(a);
+    }
 }
 
 void launch_pairdep(const Dev& d, const WalkUpd* upd) {
@@ -842,20 +974,13 @@ void launch_pairdep(const Dev& d, const WalkUpd* upd) {
     const int vn = (d.dbytes == 4) ? ((kPairVec32 == 8 && d.n % 8 == 0) ? 8 : (d.n % 4 == 0 ? 4 : 1))
                                    : (d.n % 2 == 0 ? 2 : 1);
     const int cw = kPairThreads * vn;
-    k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, (d.n + cw - 1) / cw,
-                                          d.pair_rows, d.counts + 5, d.pair_w, d.stats, d.counts + 4, d.err);
+    const int nchunks = (d.n + cw - 1) / cw;
+    k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows,
+                                          d.counts + 5, d.pair_w, d.stats, d.counts + 4, upd ? d.walk_ctl : nullptr,
+                                          d.err);
     if (upd) {
-        const int wgrid = d.nsm * kWalkCtasPerSm;
-        const size_t sm = walk_smem(d.n);
-        if (d.dbytes == 4) {
-            WalkArgs<int32_t> w{d.e_off, d.e_len, (const Arc<int32_t>*)d.e_arc, d.walk_list, d.walk_touched,
-                                d.walk_acc, d.counts + 4, *upd};
-            k_pairwalk<int32_t><<<wgrid, kWalkThreads, sm, d.st>>>(pair_args<int32_t>(d), w);
-        } else {
-            WalkArgs<int64_t> w{d.e_off, d.e_len, (const Arc<int64_t>*)d.e_arc, d.walk_list, d.walk_touched,
-                                d.walk_acc, d.counts + 4, *upd};
-            k_pairwalk<int64_t><<<wgrid, kWalkThreads, sm, d.st>>>(pair_args<int64_t>(d), w);
-        }
+        if (d.dbytes == 4) launch_walks<int32_t>(d, *upd, nchunks, vn);
+        else launch_walks<int64_t>(d, *upd, nchunks, vn);
         return;
     }
     const int grid = d.nsm * kPairCtasPerSm;   // one resident wave; later pieces go to the first free CTA

@@ -46,7 +46,7 @@ def test_binding_loads_and_sets_signatures():
 def test_record_layouts():
     assert binding.UPDATE_DTYPE.itemsize == 32
     assert binding.VEDGE_DTYPE.itemsize == 16
-    assert ctypes.sizeof(binding.bc_info) == 152
+    assert ctypes.sizeof(binding.bc_info) == 176
 
 
 def test_last_error_without_handle_is_empty_or_text():
