@@ -89,6 +89,15 @@ def test_walk_decrease_on_a_shortest_path():
     _walk_vs_test(g, ups, "i32", "decreases on path edges")
 
 
+def test_walk_long_paths_rows_for_whole_ctas():
+    # closing a long unit path into a cycle: rows with up to the cap of changed targets,
+    # each on a long path, so their walks find far more vertices than one warp takes
+    g = synth.path_graph(300, False, 1)
+    ups = [("edge", 0, 299, 1), ("edge", 100, 200, 3), ("edge", 50, 250, 1)]
+    info = _walk_vs_test(g, ups, "i32", "path closed into a cycle")
+    assert info["walk_pairs"] > 0 and info["walk_vertices"] > 0
+
+
 def test_walk_long_stream():
     g = synth.barabasi_albert(400, 3, 1, 30, 8181)
     ups = synth.update_stream(g, 40, 40, 20, 8282, 1, 30, kmin=1, kmax=5)
