@@ -688,7 +688,7 @@ struct WalkArgs {
 };
 
 constexpr int kWalkWarps = kWalkThreads / 32;
-constexpr int kWalkGrab = 4;         // units a warp takes at a time
+constexpr int kWalkGrab = 1;         // units a warp takes at a time (unit costs vary too much for more)
 
 // d(s,x) of a state: the saved value where the pair changed in this update (old state).
 template <typename DT>
@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
                                         for (int e = 0; e < w.upd.k; ++e)
                                             if (w.upd.x[e] == o) wv = w.upd.wold[e];
                                     }
-                                    if (x >= 0 && x != s && wv >= 0) {
+                                    if (x >= 0 && x != s && wv >= 0 && wv <= dyj) {   // else no predecessor
                                         const int64_t dx = walk_d<DT>(a, rs, s, x, is_new);
                                         if (dx != INF && dx + wv == dyj) {
                                             const uint32_t bit = 1u << (x & 31);
