@@ -424,10 +424,12 @@ int walk_alloc(bc_graph* g) {
     if ((rc = dalloc(g, &d.walk_list, (size_t)walk_warps(d.nsm) * n)) ||
         (rc = dalloc(g, &d.walk_buf, (size_t)d.walk_cap)) || (rc = dalloc(g, &d.walk_useg, n * kPairCap * 4)) ||
         (rc = dalloc(g, &d.walk_acc2, (size_t)walk_ctas(d.nsm) * 2 * n)) ||
-        (rc = dalloc(g, &d.walk_tl, (size_t)walk_ctas(d.nsm) * n)) || (rc = dalloc(g, &d.walk_ctl, 8)))
+        (rc = dalloc(g, &d.walk_tl, (size_t)walk_ctas(d.nsm) * n)) || (rc = dalloc(g, &d.walk_ctl, 8)) ||
+        (rc = dalloc(g, &d.walk_rowE, n)))
         return rc;
     cudaError_t e = cudaMemsetAsync(d.walk_acc2, 0, sizeof(int64_t) * (size_t)walk_ctas(d.nsm) * 2 * n, d.st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.walk_ctl, 0, sizeof(int32_t) * 8, d.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.walk_rowE, 0, sizeof(int32_t) * n, d.st);
     if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
     return BC_OK;
 }

@@ -205,6 +205,7 @@ struct Dev {
     int64_t* walk_acc2;      // [walk CTAs * 2n] per-CTA fixed-point column sums of a row (zero between rows)
     int32_t* walk_tl;        // [walk CTAs * n] per-CTA touched columns of a row
     int32_t* walk_ctl;       // [8] units and rows handed out, buffer used (64-bit), overflow
+    int32_t* walk_rowE;      // [n] per listed row: vertices found by its walks
     int64_t* bcfix;      // [2n] BC change of the corrected rows in this update, per column a
                          // fixed-point pair (units of 2^-24, units of 2^-56); zero between updates
     cudaStream_t st;

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
                                                        const int32_t* tcnt, int tcap, int nchunks,
                                                        int32_t* prows, int32_t* pcount,
                                                        int64_t* wpre, int64_t* stats, int32_t* next_piece,
-                                                       int32_t* walk_ctl, const int32_t* err) {
+                                                       int32_t* walk_ctl, int32_t* walk_rowE, const int32_t* err) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total;
     __shared__ int64_t s_rows[32], s_tgts[32];
@@ -273,6 +273,8 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
     }
     __syncthreads();
     const int cnt = s_hist[0];
+    if (walk_rowE)
+        for (int i = tid; i < cnt_all; i += blockDim.x) walk_rowE[i] = 0;
     for (int i = tid; i < cnt_all; i += blockDim.x) {
         const int r = rows[i];
         const int T = tcnt[r];
@@ -682,6 +684,8 @@ struct WalkArgs {
     int64_t* acc2;      // [CTAs * 2n] per CTA: fixed-point column sums of a row (zero between rows)
     int32_t* tl;        // [CTAs * n] per CTA: columns of the row with a sum
     int32_t* ctl;       // [0] units handed out [1] rows handed out [2..3] buffer used (64-bit) [4] overflow
+                        // [5] light rows handed out
+    int32_t* rowE;      // [n] per listed row: vertices its walks found (zeroed by k_pair_weights)
     int64_t* stats;     // [10] pairs walked [11] vertices found [12] arcs examined
     int nchunks;        // items per row in the weight prefix wpre
     WalkUpd upd;
@@ -689,6 +693,7 @@ struct WalkArgs {
 
 constexpr int kWalkWarps = kWalkThreads / 32;
 constexpr int kWalkGrab = 1;         // units a warp takes at a time (unit costs vary too much for more)
+constexpr int kWalkLightRowMax = 128;   // rows whose walks found at most this many vertices: k_walk_rows_light
 
 // d(s,x) of a state: the saved value where the pair changed in this update (old state).
 template <typename DT>
@@ -845,7 +850,10 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
                     for (int i = lane; i < tail; i += 32) vis[list[i] >> 5] = 0u;
                     __syncwarp();
                 }
-                if (lane == 0) w.useg[id * 4 + 2 * stt + 1] = found;
+                if (lane == 0) {
+                    w.useg[id * 4 + 2 * stt + 1] = found;
+                    if (found) atomicAdd(w.rowE + L, found);
+                }
             }
         }
     }
@@ -883,6 +891,10 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(P
         __syncthreads();
         const int r = s_r;
         if (r >= cnt) break;
+        if (w.rowE[r] <= kWalkLightRowMax) {   // none found, or a light row (k_walk_rows_light)
+            __syncthreads();
+            continue;
+        }
         const int s = a.prows[r];
         const int T = a.tcnt[s];
         const int64_t id0 = unit_start<DT>(a, w.nchunks, r);
@@ -932,6 +944,103 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(P
     }
 }
 
+// The rows whose walks found at most kWalkLightRowMax vertices (most rows: one to three
+// changed targets) in small CTAs, 32 per SM, so that many rows are in flight: the two
+// warps share out the row's walks and add the terms to a hash table of fixed-point
+// column sums in shared memory (kLightHash slots, at least twice the vertices, so it
+// never fills and every probe ends), which is then added to delta_s and to BC's change
+// and emptied.
+constexpr int kLightThreads = 64;
+constexpr int kLightCtasPerSm = 32;
+constexpr int kLightHash = 256;
+static_assert(kLightHash >= 2 * kWalkLightRowMax, "the light rows' hash table stays at most half full");
+
+template <typename DT>
+__global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_light(PairArgs<DT> a, WalkArgs<DT> w) {
+    __shared__ int32_t hkey[kLightHash];
+    __shared__ unsigned long long hval[2 * kLightHash];
+    __shared__ int32_t hused[kWalkLightRowMax];
+    __shared__ int s_r, s_nu;
+    if (*a.err) return;
+    if (*(volatile int32_t*)(w.ctl + 4)) return;   // overflow: the column test does the update
+    const int n = a.n;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    constexpr int kW = kLightThreads / 32;
+    for (int i = tid; i < kLightHash; i += kLightThreads) {
+        hkey[i] = -1;
+        hval[2 * i] = 0ull;
+        hval[2 * i + 1] = 0ull;
+    }
+    const int cnt = *a.pcount;
+    for (;;) {
+        if (tid == 0) {
+            s_r = atomicAdd(w.ctl + 5, 1);
+            s_nu = 0;
+        }
+        __syncthreads();
+        const int r = s_r;
+        if (r >= cnt) break;
+        const int e = w.rowE[r];
+        if (e == 0 || e > kWalkLightRowMax) {   // nothing found / taken by a whole CTA
+            __syncthreads();
+            continue;
+        }
+        const int s = a.prows[r];
+        const int T = a.tcnt[s];
+        const int64_t id0 = unit_start<DT>(a, w.nchunks, r);
+        const size_t rs = (size_t)s * n;
+        for (int q = wib; q < 2 * T; q += kW) {
+            const int u = q >> 1;
+            const bool is_new = q & 1;
+            const PairTgt& pt = a.plan[(size_t)s * a.tcap + u];
+            const int64_t base = w.useg[(id0 + u) * 4 + 2 * (q & 1)];
+            const int len = w.useg[(id0 + u) * 4 + 2 * (q & 1) + 1];
+            const ff rcp = is_new ? pt.rnew : pt.rold;
+            const size_t rt = (size_t)pt.t * n;
+            for (int i = lane; i < len; i += 32) {
+                const int x = w.buf[base + i];
+                ff term = pair_term(walk_sigma<DT>(a, rs, s, x, is_new), walk_sigma<DT>(a, rt, pt.t, x, is_new), rcp);
+                if (!is_new) term = ff{-term.hi, -term.lo};
+                long long A, B;
+                fix_split(term, &A, &B);
+                int slot = (int)(((uint32_t)x * 2654435761u) >> 24) & (kLightHash - 1);
+                for (;;) {
+                    const int old = atomicCAS(&hkey[slot], -1, x);
+                    if (old == -1) {
+                        hused[atomicAdd(&s_nu, 1)] = slot;
+                        break;
+                    }
+                    if (old == x) break;
+                    slot = (slot + 1) & (kLightHash - 1);
+                }
+                atomicAdd(&hval[2 * slot], (unsigned long long)A);
+                if (B) atomicAdd(&hval[2 * slot + 1], (unsigned long long)B);
+            }
+        }
+        __syncthreads();
+        const int nu = s_nu;
+        for (int i = tid; i < nu; i += kLightThreads) {
+            const int slot = hused[i];
+            const int x = hkey[slot];
+            const long long A0 = (long long)hval[2 * slot], B0 = (long long)hval[2 * slot + 1];
+            hkey[slot] = -1;
+            hval[2 * slot] = 0ull;
+            hval[2 * slot + 1] = 0ull;
+            const long long A = A0 + (B0 >> 32), B = B0 & 0xFFFFFFFFll;
+            const double hi = (double)A * 0x1p-24, lo = (double)B * 0x1p-56;
+            const double sum = hi + lo;
+            const float f1 = (float)sum;
+            const ff v{f1, (float)((sum - (double)f1) + ((hi - sum) + lo))};
+            ff* p = a.Dl + rs + x;
+            *p = ff_add(*p, v);
+            unsigned long long* bp = reinterpret_cast<unsigned long long*>(a.bcfix + 2 * (size_t)x);
+            atomicAdd(bp, (unsigned long long)A0);
+            if (B0) atomicAdd(bp + 1, (unsigned long long)B0);
+        }
+        __syncthreads();
+    }
+}
+
 size_t walk_smem(int n) { return (size_t)kWalkWarps * (size_t)((n + 31) / 32) * sizeof(uint32_t); }
 int64_t walk_warps(int nsm) { return (int64_t)nsm * kWalkCtasPerSm * kWalkWarps; }
 int64_t walk_ctas(int nsm) { return (int64_t)nsm * kWalkRowCtasPerSm; }
@@ -949,9 +1058,10 @@ template <typename DT>
 static void launch_walks(const Dev& d, const WalkUpd& upd, int nchunks, int vn) {
     const int grid = d.nsm * kWalkCtasPerSm, rgrid = d.nsm * kWalkRowCtasPerSm;
     WalkArgs<DT> w{d.e_off, d.e_len, (const Arc<DT>*)d.e_arc, d.walk_list, d.walk_buf, d.walk_cap, d.walk_useg,
-                   d.walk_acc2, d.walk_tl, d.walk_ctl, d.stats, nchunks, upd};
+                   d.walk_acc2, d.walk_tl, d.walk_ctl, d.walk_rowE, d.stats, nchunks, upd};
     k_walk_units<DT><<<grid, kWalkThreads, walk_smem(d.n), d.st>>>(pair_args<DT>(d), w);
     k_walk_rows<DT><<<rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), d.st>>>(pair_args<DT>(d), w);
+    k_walk_rows_light<DT><<<d.nsm * kLightCtasPerSm, kLightThreads, 0, d.st>>>(pair_args<DT>(d), w);
     // the column test, which does nothing unless the walks' buffer overflowed
     PairArgs<DT> a = pair_args<DT>(d);
     a.gate = d.walk_ctl + 4;
@@ -977,7 +1087,7 @@ void launch_pairdep(const Dev& d, const WalkUpd* upd) {
     const int nchunks = (d.n + cw - 1) / cw;
     k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows,
                                           d.counts + 5, d.pair_w, d.stats, d.counts + 4, upd ? d.walk_ctl : nullptr,
-                                          d.err);
+                                          upd ? d.walk_rowE : nullptr, d.err);
     if (upd) {
         if (d.dbytes == 4) launch_walks<int32_t>(d, *upd, nchunks, vn);
         else launch_walks<int64_t>(d, *upd, nchunks, vn);
