@@ -54,7 +54,9 @@ __global__ void k_bc_partial(int n, const int32_t* rows, const int32_t* count, c
                              ff* partial, const int32_t* err) {
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    dev_bc_partial(t, blockIdx.y, n, rows, rows ? *count : n, Dl, partial);
+    const int total = rows ? *count : n;
+    for (int rb = blockIdx.y; rb * kRowsPerBlock < total; rb += gridDim.y)
+        dev_bc_partial(t, rb, n, rows, total, Dl, partial);
 }
 
 // The same partial sums for two adjacent columns per thread (n even): 16-byte loads of
@@ -66,29 +68,30 @@ __global__ void __launch_bounds__(256) k_bc_partial2(int n, const int32_t* rows,
                                                      const ff* Dl, ff* partial, const int32_t* err) {
     if (*err) return;
     const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int rb = blockIdx.y;
     const int total = rows ? *count : n;
-    const int r0 = rb * kRowsPerBlock;
-    if (r0 >= total || t >= n) return;
-    const int r1 = min(total, r0 + kRowsPerBlock);
-    ff a0{0.0f, 0.0f}, a1{0.0f, 0.0f};
-    for (int r = r0; r < r1; r += kBcUnroll) {
-        int sr[kBcUnroll];
-        float4 v[kBcUnroll];
+    if (t >= n) return;
+    for (int rb = blockIdx.y; rb * kRowsPerBlock < total; rb += gridDim.y) {
+        const int r0 = rb * kRowsPerBlock;
+        const int r1 = min(total, r0 + kRowsPerBlock);
+        ff a0{0.0f, 0.0f}, a1{0.0f, 0.0f};
+        for (int r = r0; r < r1; r += kBcUnroll) {
+            int sr[kBcUnroll];
+            float4 v[kBcUnroll];
 #pragma unroll
-        for (int k = 0; k < kBcUnroll; ++k) sr[k] = r + k < r1 ? (rows ? rows[r + k] : r + k) : -1;
+            for (int k = 0; k < kBcUnroll; ++k) sr[k] = r + k < r1 ? (rows ? rows[r + k] : r + k) : -1;
 #pragma unroll
-        for (int k = 0; k < kBcUnroll; ++k)
-            if (sr[k] >= 0) v[k] = __ldcs(reinterpret_cast<const float4*>(Dl + (size_t)sr[k] * n + t));
+            for (int k = 0; k < kBcUnroll; ++k)
+                if (sr[k] >= 0) v[k] = __ldcs(reinterpret_cast<const float4*>(Dl + (size_t)sr[k] * n + t));
 #pragma unroll
-        for (int k = 0; k < kBcUnroll; ++k) {
-            if (sr[k] < 0) break;
-            if (sr[k] != t) a0 = ff_add(a0, ff{v[k].x, v[k].y});
-            if (sr[k] != t + 1) a1 = ff_add(a1, ff{v[k].z, v[k].w});
+            for (int k = 0; k < kBcUnroll; ++k) {
+                if (sr[k] < 0) break;
+                if (sr[k] != t) a0 = ff_add(a0, ff{v[k].x, v[k].y});
+                if (sr[k] != t + 1) a1 = ff_add(a1, ff{v[k].z, v[k].w});
+            }
         }
+        partial[(size_t)rb * n + t] = a0;
+        partial[(size_t)rb * n + t + 1] = a1;
     }
-    partial[(size_t)rb * n + t] = a0;
-    partial[(size_t)rb * n + t + 1] = a1;
 }
 
 __global__ void k_bc_finish(int n, const int32_t* rows, const int32_t* count, const ff* partial,
@@ -174,11 +177,18 @@ void launch_accum_rows(const Dev& d, const int32_t* rows, const int32_t* count) 
 
 // sign = -1 / +1: subtract / add the rows listed in acc_rows; is_static: all rows,
 // overwriting BC.
+// The row blocks go to gridDim.y CTAs per column block in turn, about eight CTAs per SM
+// in all (the count of listed rows is known only on the device).
+static int bc_row_ctas(const Dev& d, int col_blocks) {
+    return std::max(1, std::min(d.nrb_max, d.nsm * 8 / col_blocks));
+}
+
 static void bc_rows(const Dev& d, int sign, int is_static, const int32_t* rows, const int32_t* count) {
     const int tb = (d.n + 255) / 256;
-    dim3 g1(tb, d.nrb_max);
+    dim3 g1(tb, bc_row_ctas(d, tb));
     if (d.n % 2 == 0) {
-        dim3 g2((d.n / 2 + 255) / 256, d.nrb_max);
+        const int tb2 = (d.n / 2 + 255) / 256;
+        dim3 g2(tb2, bc_row_ctas(d, tb2));
         k_bc_partial2<<<g2, 256, 0, d.st>>>(d.n, rows, count, d.Dl, d.partial, d.err);
     } else {
         k_bc_partial<<<g1, 256, 0, d.st>>>(d.n, rows, count, d.Dl, d.partial, d.err);

@@ -40,19 +40,25 @@ __global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt,
 }
 
 // Per-update records of the rows listed in rows[0..count) back to zero (a pair (s,t)
-// changes only in a changed row s); the rows sent to the full path are added to
-// stats[7].
-__global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t* tcnt, uint32_t* chg, int words,
-                             const int32_t* full_count, int64_t* stats) {
+// changes only in a changed row s), a warp per row: a row with at most tcap changed
+// targets has its bits only in the words of its listed targets, a longer one is
+// cleared whole.  The rows sent to the full path are added to stats[7].
+__global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t* tcnt, const int32_t* tlist,
+                             int tcap, uint32_t* chg, int words, const int32_t* full_count, int64_t* stats) {
     const int cnt = *count;
     if (blockIdx.x == 0 && threadIdx.x == 0) stats[7] += *full_count;
-    const int64_t total = (int64_t)cnt * words;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(j / words), w = (int)(j - (int64_t)i * words);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < cnt; i += gridDim.x * wpb) {
         const int s = rows[i];
-        chg[(size_t)s * words + w] = 0u;
-        if (w == 0) tcnt[s] = 0;
+        const int T = tcnt[s];
+        uint32_t* row = chg + (size_t)s * words;
+        if (T <= tcap) {
+            for (int j = lane; j < T; j += 32) row[tlist[(size_t)s * tcap + j] >> 5] = 0u;
+        } else {
+            for (int j = lane; j < words; j += 32) row[j] = 0u;
+        }
+        __syncwarp();
+        if (lane == 0) tcnt[s] = 0;
     }
 }
 
@@ -282,39 +288,44 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
     }
     __syncthreads();
     int64_t my_rows = 0, my_tgts = 0;
-    int64_t base = 0;
-    for (int tile = 0; tile < cnt; tile += blockDim.x) {
-        const int i = tile + tid;
-        const int64_t iw = i < cnt ? item_weight(tcnt[prows[i]], tcap) : 0;
+    // a run of consecutive rows per thread: the runs' weights are scanned once for the block
+    const int per = (cnt + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = min(cnt, tid * per), i1 = min(cnt, i0 + per);
+    int64_t mine = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int64_t iw = item_weight(tcnt[prows[i]], tcap);
         if (iw) {
             ++my_rows;
             my_tgts += iw - 1;
         }
-        const int64_t w = iw * nchunks;
-        int64_t incl = w;
+        mine += iw * nchunks;
+    }
+    int64_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int64_t x = lane < nw ? wsum[lane] : 0;
+        int64_t winc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            const int64_t y = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += y;
         }
-        if (lane == 31) wsum[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            const int64_t x = lane < nw ? wsum[lane] : 0;
-            int64_t winc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(0xffffffffu, winc, o);
-                if (lane >= o) winc += y;
-            }
-            if (lane < nw) wsum[lane] = winc - x;
-            if (lane == 31) s_total = winc;
-        }
-        __syncthreads();
-        if (i < cnt) wpre[i] = base + wsum[wid] + incl - w;
-        base += s_total;
-        __syncthreads();
+        if (lane < nw) wsum[lane] = winc - x;
+        if (lane == 31) s_total = winc;
     }
+    __syncthreads();
+    int64_t off = wsum[wid] + incl - mine;
+    for (int i = i0; i < i1; ++i) {
+        wpre[i] = off;
+        off += item_weight(tcnt[prows[i]], tcap) * nchunks;
+    }
+    const int64_t base = s_total;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         my_rows += __shfl_xor_sync(0xffffffffu, my_rows, o);
@@ -620,8 +631,8 @@ void launch_full_flags(const Dev& d) {
 }
 
 void launch_pair_clear(const Dev& d) {
-    k_pair_clear<<<d.nsm * 4, 256, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.chg, d.chg_words,
-                                              d.counts + 3, d.stats);
+    k_pair_clear<<<d.nsm * 4, 256, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tlist, d.tcap, d.chg,
+                                              d.chg_words, d.counts + 3, d.stats);
 }
 
 template <typename DT>
@@ -742,11 +753,12 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
         g0 = __shfl_sync(0xffffffffu, g0, 0);
         if (g0 >= nunits) break;
         for (int64_t id = g0; id < min((int64_t)g0 + kWalkGrab, nunits); ++id) {
-            // the unit's row: the last r with unit_start(r) <= id
+            // the unit's row: the last r with unit_start(r) <= id, i.e. wpre[r] <= (id + r) *
+            // nchunks (wpre[r] is a multiple of nchunks)
             int L = 0, R = cnt;
             while (R - L > 1) {
                 const int m = (L + R) >> 1;
-                if (unit_start<DT>(a, w.nchunks, m) <= id) L = m; else R = m;
+                if (a.wpre[m] <= (id + m) * w.nchunks) L = m; else R = m;
             }
             const int s = a.prows[L];
             const int u = (int)(id - unit_start<DT>(a, w.nchunks, L));
@@ -784,12 +796,13 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
                             }
                             const int tot = __shfl_sync(0xffffffffu, incl, 31);
                             const int excl = incl - len;
+                            // first step of the owner search: the largest power of two below nb
+                            const int top = nb > 1 ? 1 << (31 - __clz(nb - 1)) : 0;
                             n_arcs += tot;
                             for (int k0 = 0; k0 < tot; k0 += 32) {   // the batch's arcs, one per lane
                                 const int k = k0 + lane;
                                 int j = 0;   // owner: the last lane j < nb whose arcs start at or before k
-#pragma unroll
-                                for (int step = 16; step >= 1; step >>= 1) {
+                                for (int step = top; step >= 1; step >>= 1) {
                                     const int c = j + step;
                                     const int ex = __shfl_sync(0xffffffffu, excl, c & 31);
                                     if (c < nb && ex <= k) j = c;
