@@ -876,12 +876,30 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
     }
 }
 
-// A term as a fixed-point pair (units of 2^-24, 2^-56), as in bc_fix_add.
+// A term v = hi + lo (|v| <= 1 + 2^-40, a pair dependency) as a fixed-point pair (units
+// of 2^-24 and 2^-56, as in bc_fix_add) in single precision only (fp64 runs at a small
+// fraction of the fp32 rate here): with h = hi * 2^24 and a = rint(h), h - a is exact
+// (|h| <= 2^24 + 1), and (h - a) * 2^32 and lo * 2^56 are exact scalings, each rounded to
+// an integer once, so B is within one unit of v * 2^56 - A * 2^32; a carry keeps
+// |B| <= 2^31.
 __device__ __forceinline__ void fix_split(ff v, long long* A, long long* B) {
-    const double vd = ((double)v.hi + (double)v.lo) * 0x1p24;
-    const double a = rint(vd);
-    *A = (long long)a;
-    *B = __double2ll_rn((vd - a) * 0x1p32);
+    const float h = v.hi * 0x1p24f;
+    const float a = rintf(h);
+    long long b = __float2ll_rn((h - a) * 0x1p32f) + __float2ll_rn(v.lo * 0x1p56f);
+    const long long c = (b + (1ll << 31)) >> 32;
+    *A = (long long)__float2int_rn(a) + c;
+    *B = b - (c << 32);
+}
+
+// A column's fixed-point sum (A in units of 2^-24 plus B in units of 2^-56, 0 <= B <
+// 2^32, |A| < 2^47) as a float-float: four exactly representable parts, added with
+// error-free sums.
+__device__ __forceinline__ ff fix_to_ff(long long A, long long B) {
+    const float p0 = (float)(int)(A >> 24);
+    const float p1 = (float)(int)(A & 0xFFFFFF) * 0x1p-24f;
+    const float p2 = (float)(int)(B >> 24) * 0x1p-32f;
+    const float p3 = (float)(int)(B & 0xFFFFFF) * 0x1p-56f;
+    return ff_add(two_sum(p0, p1), two_sum(p2, p3));
 }
 
 template <typename DT>
@@ -941,11 +959,7 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(P
             const long long A0 = acc[2 * x], B0 = acc[2 * x + 1];
             acc[2 * x] = 0;
             acc[2 * x + 1] = 0;
-            const long long A = A0 + (B0 >> 32), B = B0 & 0xFFFFFFFFll;
-            const double hi = (double)A * 0x1p-24, lo = (double)B * 0x1p-56;
-            const double sum = hi + lo;
-            const float f1 = (float)sum;
-            const ff v{f1, (float)((sum - (double)f1) + ((hi - sum) + lo))};
+            const ff v = fix_to_ff(A0 + (B0 >> 32), B0 & 0xFFFFFFFFll);
             ff* p = a.Dl + rs + x;
             *p = ff_add(*p, v);
             unsigned long long* bp = reinterpret_cast<unsigned long long*>(a.bcfix + 2 * (size_t)x);
@@ -1039,11 +1053,7 @@ __global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_li
             hkey[slot] = -1;
             hval[2 * slot] = 0ull;
             hval[2 * slot + 1] = 0ull;
-            const long long A = A0 + (B0 >> 32), B = B0 & 0xFFFFFFFFll;
-            const double hi = (double)A * 0x1p-24, lo = (double)B * 0x1p-56;
-            const double sum = hi + lo;
-            const float f1 = (float)sum;
-            const ff v{f1, (float)((sum - (double)f1) + ((hi - sum) + lo))};
+            const ff v = fix_to_ff(A0 + (B0 >> 32), B0 & 0xFFFFFFFFll);
             ff* p = a.Dl + rs + x;
             *p = ff_add(*p, v);
             unsigned long long* bp = reinterpret_cast<unsigned long long*>(a.bcfix + 2 * (size_t)x);
