@@ -497,11 +497,7 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
     if (pair) {
         // rows with more changed targets than kPairCap (and row v): Algorithm 1 in full;
         // the others: pair corrections of their dependency rows
-        timed(g, 4, 2, [&] {
-            launch_full_flags(d);
-            launch_compact(d, d.mark, 1, d.full_rows, d.counts + 3, 0, 0);
-        });
-        timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
+        timed(g, 4, 1, [&] { launch_pair_lists(d); });
         // BC: the full rows are subtracted before and added after their re-accumulation;
         // the corrected rows add their changes to BC as they are made (k_pairdep)
         timed(g, 2, 2, [&] { launch_bc_rows_list(d, -1, d.full_rows, d.counts + 3); });

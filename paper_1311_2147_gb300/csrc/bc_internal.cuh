@@ -264,7 +264,7 @@ void launch_scan_out(const Dev& d, int32_t v);
 void launch_write_row(const Dev& d, int32_t v);
 void launch_estar_keep(const Dev& d, uint8_t* keep);
 PairRec pair_rec(const Dev& d);
-void launch_full_flags(const Dev& d);
+void launch_pair_lists(const Dev& d);
 void launch_pairdep(const Dev& d, const WalkUpd* upd);   // upd: DAG walks (k_pairwalk), else column tests
 size_t walk_smem(int n);
 int64_t walk_warps(int nsm);

@@ -33,10 +33,88 @@ template <int VN> struct PairGroup { static constexpr int value = VN >= 8 ? 1 : 
 constexpr int kPairPieces = 8;  // pieces of equal weight per CTA of the grid
 constexpr int kPairVec32 = 8;   // columns per thread with int32 distances (4 or 8)
 
-// mark[s] = row s changed and has more recorded targets than the cap.
-__global__ void k_full_flags(int n, const uint8_t* changed, const int32_t* tcnt, int tcap, uint8_t* mark) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) mark[s] = (changed[s] != 0 && tcnt[s] > tcap) ? 1 : 0;
+// The row lists of an update's corrections in one pass over the changed-row flags (one
+// CTA, kCompactPerThread flags per thread and tile, as k_compact): acc_rows = the
+// changed rows, full_rows = those with more recorded targets than the cap (Algorithm 1
+// in full), both in increasing order.  The flags are cleared and the per-update counters
+// added as k_compact does for acc_rows.  A thread's two counts travel in one scan word
+// (each tile holds at most 1024 x 16 < 2^16 rows).
+__global__ void __launch_bounds__(kCompactThreads) k_pair_lists(int n, uint8_t* changed, const int32_t* tcnt,
+                                                                int tcap, int32_t* acc_rows, int32_t* acc_count,
+                                                                int32_t* full_rows, int32_t* full_count,
+                                                                int64_t* stats, const int32_t* err) {
+    constexpr int E = kCompactPerThread;
+    static_assert(kCompactThreads * E < (1 << 16), "a tile's counts fit 16 bits");
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t s_total;
+    const int nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool bad = *err != 0;
+    int base_a = 0, base_f = 0;
+    for (int tile = 0; tile < n; tile += (int)blockDim.x * E) {
+        const int s0 = tile + tid * E;
+        uint32_t fl = 0, ffl = 0;   // bit e: row s0 + e changed / goes to the full path
+        if (s0 < n) {
+            if (s0 + E <= n && ((reinterpret_cast<uintptr_t>(changed + s0) & 15) == 0)) {
+                const uint4 v = *reinterpret_cast<const uint4*>(changed + s0);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((w[e >> 2] >> (8 * (e & 3))) & 0xFFu) fl |= 1u << e;
+                *reinterpret_cast<uint4*>(changed + s0) = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                for (int e = 0; e < E && s0 + e < n; ++e) {
+                    if (changed[s0 + e]) fl |= 1u << e;
+                    changed[s0 + e] = 0;
+                }
+            }
+            if (bad) fl = 0;
+            for (uint32_t b = fl; b; b &= b - 1) {
+                const int e = __ffs(b) - 1;
+                if (tcnt[s0 + e] > tcap) ffl |= 1u << e;
+            }
+        }
+        const int c = __popc(fl) | (__popc(ffl) << 16);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int x = lane < nwarps ? wsum[lane] : 0;
+            int winc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, winc, o);
+                if (lane >= o) winc += y;
+            }
+            if (lane < nwarps) wsum[lane] = winc - x;
+            if (lane == 31) s_total = winc;
+        }
+        __syncthreads();
+        const int excl = wsum[wid] + incl - c;
+        int pa = base_a + (excl & 0xFFFF), pf = base_f + (excl >> 16);
+        while (fl) {
+            const int e = __ffs(fl) - 1;
+            fl &= fl - 1;
+            acc_rows[pa++] = s0 + e;
+            if ((ffl >> e) & 1u) full_rows[pf++] = s0 + e;
+        }
+        base_a += s_total & 0xFFFF;
+        base_f += s_total >> 16;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *acc_count = base_a;
+        *full_count = base_f;
+        stats[0] += base_a;
+        if (base_a == 0) stats[1] += 1;
+        if (base_a > stats[2]) stats[2] = base_a;
+        stats[3] += 1;
+    }
 }
 
 // Per-update records of the rows listed in rows[0..count) back to zero (a pair (s,t)
@@ -115,29 +193,31 @@ __device__ __forceinline__ void bc_fix_add(int64_t* fix, int x, ff v) {
     if (b) atomicAdd(p + 1, (unsigned long long)b);
 }
 
-// One CTA (kPlanThreads >= tcap threads) per listed row with 1..tcap changed targets:
-// sort them (the sums then run in a fixed order) and write the per-target scalars of
-// the plan.  Every target of row s has its bit set, so its old values are the saved ones.
-constexpr int kPlanThreads = kPairCap;
+// One warp per listed row with 1..tcap changed targets (most rows have a few): rank
+// them (the sums then run in a fixed order) and write the per-target scalars of the
+// plan.  Every target of row s has its bit set, so its old values are the saved ones.
+constexpr int kPlanThreads = 256;
 
 template <typename DT>
 __global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
-    __shared__ int32_t s_val[kPlanThreads];
+    __shared__ int32_t s_val[kPlanThreads / 32][kPairCap];
     if (*a.err) return;
     const int n = a.n;
     const int64_t INF = Inf<DT>::v;
     const int cnt = *a.count;
-    const int tid = threadIdx.x;
-    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t* sv = s_val[wib];
+    const int nw = gridDim.x * (kPlanThreads / 32);
+    for (int i = blockIdx.x * (kPlanThreads / 32) + wib; i < cnt; i += nw) {
         const int s = a.rows[i];
         const int T = a.tcnt[s];
-        if (T == 0 || T > a.tcap) continue;   // block-uniform
-        const int val = tid < T ? a.tlist[(size_t)s * a.tcap + tid] : INT32_MAX;
-        s_val[tid] = val;
-        __syncthreads();
-        int pos = 0;
-        for (int j = 0; j < T; ++j) pos += s_val[j] < val;   // targets are distinct
-        if (tid < T) {
+        if (T == 0 || T > a.tcap) continue;   // warp-uniform
+        for (int j = lane; j < T; j += 32) sv[j] = a.tlist[(size_t)s * a.tcap + j];
+        __syncwarp();
+        for (int j = lane; j < T; j += 32) {
+            const int val = sv[j];
+            int pos = 0;
+            for (int k = 0; k < T; ++k) pos += sv[k] < val;   // targets are distinct
             const size_t it = (size_t)s * n + val;
             const int64_t dol = a.oD[it], dnw = a.D[it];
             const uint64_t sol = a.oS[it], snw = a.S[it];
@@ -150,7 +230,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
             p.rnew = snw ? ff_rcp(ff_from_u64(snw)) : ff{0.f, 0.f};
             a.plan[(size_t)s * a.tcap + pos] = p;
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -626,8 +706,9 @@ PairRec pair_rec(const Dev& d) {
     return r;
 }
 
-void launch_full_flags(const Dev& d) {
-    k_full_flags<<<(d.n + 255) / 256, 256, 0, d.st>>>(d.n, d.changed, d.tcnt, d.tcap, d.mark);
+void launch_pair_lists(const Dev& d) {
+    k_pair_lists<<<1, kCompactThreads, 0, d.st>>>(d.n, d.changed, d.tcnt, d.tcap, d.acc_rows, d.counts + 1,
+                                                  d.full_rows, d.counts + 3, d.stats, d.err);
 }
 
 void launch_pair_clear(const Dev& d) {
