@@ -12,29 +12,33 @@ namespace bcg {
 // Algorithm 4 (Compute-Dist-to-v) for source s = this thread, over the in-edges
 // (x_j, v) of the update, followed by the affected-row test of the IN phase: row s can
 // change only if d'(s,v) < d(s,v) or new shortest paths reach v (sigma-hat > 0).
-template <typename DT>
+// SYM: the graph is undirected and the state is the one before the update, whose d and
+// sigma are symmetric, so d(s,x) is read as d(x,s) (consecutive threads then read
+// consecutive entries of row x instead of one entry of each row).
+template <typename DT, bool SYM = false>
 __device__ __forceinline__ void dev_alg4_in(int s, int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
                           int v, const VEdge* __restrict__ e, int k, int directed,
                           DT* fD, uint64_t* fS, uint64_t* fM, uint8_t* mark, uint8_t* changed,
                           int32_t* err) {
     const int64_t INF = Inf<DT>::v;
     const size_t rs = (size_t)s * n;
-    const int64_t old = D[rs + v];
+    auto at = [&](int x) { return SYM ? (size_t)x * n + s : rs + x; };
+    const int64_t old = D[at(v)];
     int64_t cur = old;
-    uint64_t sig = S[rs + v];
+    uint64_t sig = S[at(v)];
     uint64_t hat = 0;
     bool sat = false;
     for (int j = 0; j < k; ++j) {
         const VEdge ed = e[j];
         if (directed && ed.dir != 0) continue;
-        const int64_t dx = D[rs + ed.x];
+        const int64_t dx = D[at(ed.x)];
         if (dx == INF) continue;
         const int64_t dj = dsum<DT>(dx, ed.w);
         if (dj == SAT) {
             sat = true;
             continue;
         }
-        const uint64_t sx = S[rs + ed.x];
+        const uint64_t sx = S[at(ed.x)];
         if (cur == dj) {
             sig = add_chk(sig, sx, err);
             hat += sx;

@@ -56,7 +56,9 @@ __global__ void k_alg4_in(int n, const DT* __restrict__ D, const uint64_t* __res
                           int32_t* err) {
     if (*err) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) dev_alg4_in<DT>(s, n, D, S, v, e, k, directed, fD, fS, fM, mark, changed, err);
+    if (s >= n) return;
+    if (directed) dev_alg4_in<DT, false>(s, n, D, S, v, e, k, directed, fD, fS, fM, mark, changed, err);
+    else dev_alg4_in<DT, true>(s, n, D, S, v, e, k, directed, fD, fS, fM, mark, changed, err);
 }
 
 template <typename DT>
