@@ -825,7 +825,8 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
     const int v = w.upd.v;
     // this warp's block of the buffer: [bnext, bend)
     long long bnext = 0, bend = 0;
-    long long n_found = 0, n_arcs = 0;   // counters (lane 0 adds them to stats at the end)
+    __shared__ unsigned long long s_cnt[kWalkWarps][2];   // per warp: vertices found, arcs examined
+    if (lane == 0) s_cnt[wib][0] = s_cnt[wib][1] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 10), (unsigned long long)nunits);
     for (;;) {
@@ -879,7 +880,7 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
                             const int excl = incl - len;
                             // first step of the owner search: the largest power of two below nb
                             const int top = nb > 1 ? 1 << (31 - __clz(nb - 1)) : 0;
-                            n_arcs += tot;
+                            if (lane == 0) s_cnt[wib][1] += (unsigned)tot;
                             for (int k0 = 0; k0 < tot; k0 += 32) {   // the batch's arcs, one per lane
                                 const int k = k0 + lane;
                                 int j = 0;   // owner: the last lane j < nb whose arcs start at or before k
@@ -919,7 +920,7 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
                         __syncwarp();
                     }
                     found = tail - 1;
-                    n_found += found;
+                    if (lane == 0) s_cnt[wib][0] += (unsigned)found;
                     // the walk's vertices (t excluded) into the buffer
                     // room in the warp's block, else a new block (a walk longer than a block
                     // gets a block of its own size); one atomic per block, not per walk
@@ -951,9 +952,9 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(Pai
             }
         }
     }
-    if (lane == 0 && (n_found | n_arcs)) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 11), (unsigned long long)n_found);
-        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 12), (unsigned long long)n_arcs);
+    if (lane == 0 && (s_cnt[wib][0] | s_cnt[wib][1])) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 11), s_cnt[wib][0]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.stats + 12), s_cnt[wib][1]);
     }
 }
 
