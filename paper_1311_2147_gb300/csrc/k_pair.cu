@@ -321,8 +321,10 @@ struct TgtSlow {
 __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0 || T > tcap) ? 0 : T + 1; }
 
 // prows[0..*pcount) = the listed rows with 1..tcap targets, most targets first;
-// wpre[i] = total weight of the items of rows prows[0..i-1] (nchunks items per row);
-// one CTA, a block scan per tile of rows.
+// wpre[i] = total weight of the items of rows prows[0..i-1] (nchunks items per row).
+// One CTA: a counting sort (the lanes of a warp with the same target count add to its
+// bucket with one shared-memory atomic), then each warp scans a contiguous run of the
+// sorted rows and one block scan joins the runs.
 // Also adds the rows with a correction and their targets to stats[8], stats[9].
 __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
                                                        const int32_t* tcnt, int tcap, int nchunks,
@@ -337,14 +339,18 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
     const int cnt_all = *count;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = blockDim.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     // the rows with 1..tcap targets, most targets first (a counting sort): the heaviest
     // items are handed out first and the light ones fill the end of the kernel.  The
     // order inside a bucket follows the atomics; a row's result does not depend on it.
     for (int b = tid; b <= kPairCap; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
-    for (int i = tid; i < cnt_all; i += blockDim.x) {
-        const int T = tcnt[rows[i]];
-        if (T > 0 && T <= tcap) atomicAdd(&s_hist[T], 1);
+    for (int i0 = 0; i0 < cnt_all; i0 += blockDim.x) {   // warp-uniform bounds (the match)
+        const int i = i0 + tid;
+        const int T = i < cnt_all ? tcnt[rows[i]] : 0;
+        const bool ok = T > 0 && T <= tcap;
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? T : -1);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[T], __popc(peers));
     }
     __syncthreads();
     if (tid == 0) {
@@ -361,49 +367,57 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
     const int cnt = s_hist[0];
     if (walk_rowE)
         for (int i = tid; i < cnt_all; i += blockDim.x) walk_rowE[i] = 0;
-    for (int i = tid; i < cnt_all; i += blockDim.x) {
-        const int r = rows[i];
-        const int T = tcnt[r];
-        if (T > 0 && T <= tcap) prows[atomicAdd(&s_hist[T], 1)] = r;
+    for (int i0 = 0; i0 < cnt_all; i0 += blockDim.x) {
+        const int i = i0 + tid;
+        const int r = i < cnt_all ? rows[i] : 0;
+        const int T = i < cnt_all ? tcnt[r] : 0;
+        const bool ok = T > 0 && T <= tcap;
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? T : -1);
+        const int leader = __ffs(peers) - 1;
+        int p0 = 0;
+        if (ok && lane == leader) p0 = atomicAdd(&s_hist[T], __popc(peers));
+        p0 = __shfl_sync(0xffffffffu, p0, leader);
+        if (ok) prows[p0 + __popc(peers & below)] = r;
     }
     __syncthreads();
     int64_t my_rows = 0, my_tgts = 0;
-    // a run of consecutive rows per thread: the runs' weights are scanned once for the block
-    const int per = (cnt + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int i0 = min(cnt, tid * per), i1 = min(cnt, i0 + per);
-    int64_t mine = 0;
-    for (int i = i0; i < i1; ++i) {
-        const int64_t iw = item_weight(tcnt[prows[i]], tcap);
+    // a contiguous run of the sorted rows per warp, 32 rows per step
+    const int per = (cnt + nw - 1) / nw;
+    const int w0 = min(cnt, wid * per), w1 = min(cnt, w0 + per);
+    auto warp_incl = [&](int64_t x) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        return x;
+    };
+    int64_t run = 0;
+    for (int b0 = w0; b0 < w1; b0 += 32) {
+        const int i = b0 + lane;
+        const int64_t iw = i < w1 ? item_weight(tcnt[prows[i]], tcap) : 0;
         if (iw) {
             ++my_rows;
             my_tgts += iw - 1;
         }
-        mine += iw * nchunks;
+        run += __shfl_sync(0xffffffffu, warp_incl(iw * nchunks), 31);
     }
-    int64_t incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[wid] = incl;
+    if (lane == 0) wsum[wid] = run;
     __syncthreads();
     if (wid == 0) {
         const int64_t x = lane < nw ? wsum[lane] : 0;
-        int64_t winc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, winc, o);
-            if (lane >= o) winc += y;
-        }
+        const int64_t winc = warp_incl(x);
         if (lane < nw) wsum[lane] = winc - x;
         if (lane == 31) s_total = winc;
     }
     __syncthreads();
-    int64_t off = wsum[wid] + incl - mine;
-    for (int i = i0; i < i1; ++i) {
-        wpre[i] = off;
-        off += item_weight(tcnt[prows[i]], tcap) * nchunks;
+    run = wsum[wid];
+    for (int b0 = w0; b0 < w1; b0 += 32) {
+        const int i = b0 + lane;
+        const int64_t x = i < w1 ? item_weight(tcnt[prows[i]], tcap) * nchunks : 0;
+        const int64_t incl = warp_incl(x);
+        if (i < w1) wpre[i] = run + incl - x;
+        run += __shfl_sync(0xffffffffu, incl, 31);
     }
     const int64_t base = s_total;
 #pragma unroll
