@@ -182,8 +182,9 @@ struct PairArgs {
 // does not depend on the order in which rows and CTAs add (the result is deterministic)
 // and is exact up to the 2^-57 rounding of each entry.  Bounds: each pair term
 // delta_st(x) lies in [0, 1] and a row has at most kPairCap targets, so |v| <= 128 and
-// |A| <= 2^31, |B| <= 2^31 per entry; a column receives at most one entry per row, so
-// for n < 2^21 both sums stay below 2^52 and k_bc_fix converts them exactly.
+// |A| <= 2^31, |B| <= 2^31 per entry (the DAG walks add a row's column sum with
+// 0 <= B < 2^32); a column receives at most one entry per row, so for n < 2^20 both
+// sums stay below 2^52 and k_bc_fix converts them exactly.
 __device__ __forceinline__ void bc_fix_add(int64_t* fix, int x, ff v) {
     const double vd = ((double)v.hi + (double)v.lo) * 0x1p24;   // exact
     const double a = rint(vd);
@@ -790,7 +791,7 @@ struct WalkArgs {
     int64_t* acc2;      // [CTAs * 2n] per CTA: fixed-point column sums of a row (zero between rows)
     int32_t* tl;        // [CTAs * n] per CTA: columns of the row with a sum
     int32_t* ctl;       // [0] units handed out [1] rows handed out [2..3] buffer used (64-bit) [4] overflow
-                        // [5] light rows handed out
+                        // [5] light rows handed out [6] mid-size rows handed out
     int32_t* rowE;      // [n] per listed row: vertices its walks found (zeroed by k_pair_weights)
     int64_t* stats;     // [10] pairs walked [11] vertices found [12] arcs examined
     int nchunks;        // items per row in the weight prefix wpre
@@ -799,7 +800,8 @@ struct WalkArgs {
 
 constexpr int kWalkWarps = kWalkThreads / 32;
 constexpr int kWalkGrab = 1;         // units a warp takes at a time (unit costs vary too much for more)
-constexpr int kWalkLightRowMax = 128;   // rows whose walks found at most this many vertices: k_walk_rows_light
+constexpr int kWalkLightRowMax = 128;   // rows whose walks found at most this many vertices: light CTAs
+constexpr int kWalkMidRowMax = 1024;    // up to this many: mid-size CTAs; more: k_walk_rows
 
 // d(s,x) of a state: the saved value where the pair changed in this update (old state).
 template <typename DT>
@@ -1018,7 +1020,7 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(P
         __syncthreads();
         const int r = s_r;
         if (r >= cnt) break;
-        if (w.rowE[r] <= kWalkLightRowMax) {   // none found, or a light row (k_walk_rows_light)
+        if (w.rowE[r] <= kWalkMidRowMax) {   // none found, or taken by k_walk_rows_hash
             __syncthreads();
             continue;
         }
@@ -1055,41 +1057,55 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(P
             const long long A0 = acc[2 * x], B0 = acc[2 * x + 1];
             acc[2 * x] = 0;
             acc[2 * x + 1] = 0;
-            const ff v = fix_to_ff(A0 + (B0 >> 32), B0 & 0xFFFFFFFFll);
+            const long long A = A0 + (B0 >> 32), B = B0 & 0xFFFFFFFFll;   // 0 <= B < 2^32
+            const ff v = fix_to_ff(A, B);
             ff* p = a.Dl + rs + x;
             *p = ff_add(*p, v);
             unsigned long long* bp = reinterpret_cast<unsigned long long*>(a.bcfix + 2 * (size_t)x);
-            atomicAdd(bp, (unsigned long long)A0);
-            if (B0) atomicAdd(bp + 1, (unsigned long long)B0);
+            atomicAdd(bp, (unsigned long long)A);
+            if (B) atomicAdd(bp + 1, (unsigned long long)B);
             tbits[x >> 5] = 0u;
         }
         __syncthreads();
     }
 }
 
-// The rows whose walks found at most kWalkLightRowMax vertices (most rows: one to three
-// changed targets) in small CTAs, 32 per SM, so that many rows are in flight: the two
-// warps share out the row's walks and add the terms to a hash table of fixed-point
-// column sums in shared memory (kLightHash slots, at least twice the vertices, so it
-// never fills and every probe ends), which is then added to delta_s and to BC's change
-// and emptied.
-constexpr int kLightThreads = 64;
-constexpr int kLightCtasPerSm = 32;
-constexpr int kLightHash = 256;
-static_assert(kLightHash >= 2 * kWalkLightRowMax, "the light rows' hash table stays at most half full");
+// The rows whose walks found at most kMaxE vertices (and more than kMinE) in CTAs of
+// kThreads threads, many per SM so that many rows are in flight: the warps share out the
+// row's walks and add the terms to a hash table of fixed-point column sums in shared
+// memory (kHash slots, at least twice the vertices, so it never fills and every probe
+// ends), which is then added to delta_s and to BC's change and emptied.  Two classes:
+// light rows (at most 128 vertices; most rows, one to three changed targets) in 64-thread
+// CTAs, 32 per SM, and mid-size rows (129 to 1024 vertices) in 256-thread CTAs with a
+// 2048-slot table, 4 per SM.  Rows with more vertices go to k_walk_rows.
+template <int kThreads, int kCtas, int kHash, int kMinE, int kMaxE, int kCtl>
+struct WalkHash {
+    static constexpr int threads = kThreads, ctas = kCtas, hash = kHash, min_e = kMinE, max_e = kMaxE, ctl = kCtl;
+    static_assert(kHash >= 2 * kMaxE, "the hash table stays at most half full");
+    static_assert((kHash & (kHash - 1)) == 0, "a power of two");
+    static constexpr int bits = kHash == 256 ? 8 : kHash == 512 ? 9 : kHash == 1024 ? 10 : kHash == 2048 ? 11 : 12;
+    static_assert((1 << bits) == kHash, "table size");
+    static constexpr size_t smem = (size_t)kHash * (2 * sizeof(unsigned long long) + sizeof(int32_t)) +
+                                   (size_t)kMaxE * sizeof(int32_t);
+};
+using WalkLight = WalkHash<64, 32, 256, 0, kWalkLightRowMax, 5>;
+using WalkMid = WalkHash<256, 4, 2048, kWalkLightRowMax, kWalkMidRowMax, 6>;
+static_assert(WalkMid::smem * WalkMid::ctas <= 200 * 1024, "mid-size tables fit the SM");
+static_assert(WalkMid::smem <= 48 * 1024 && WalkLight::smem <= 48 * 1024, "no opt-in shared memory needed");
 
-template <typename DT>
-__global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_light(PairArgs<DT> a, WalkArgs<DT> w) {
-    __shared__ int32_t hkey[kLightHash];
-    __shared__ unsigned long long hval[2 * kLightHash];
-    __shared__ int32_t hused[kWalkLightRowMax];
+template <typename DT, typename H>
+__global__ void __launch_bounds__(H::threads, H::ctas) k_walk_rows_hash(PairArgs<DT> a, WalkArgs<DT> w) {
+    extern __shared__ unsigned long long hsm[];
+    unsigned long long* hval = hsm;                                        // [2 * hash]
+    int32_t* hkey = reinterpret_cast<int32_t*>(hsm + 2 * H::hash);         // [hash]
+    int32_t* hused = hkey + H::hash;                                       // [max_e]
     __shared__ int s_r, s_nu;
     if (*a.err) return;
     if (*(volatile int32_t*)(w.ctl + 4)) return;   // overflow: the column test does the update
     const int n = a.n;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    constexpr int kW = kLightThreads / 32;
-    for (int i = tid; i < kLightHash; i += kLightThreads) {
+    constexpr int kW = H::threads / 32;
+    for (int i = tid; i < H::hash; i += H::threads) {
         hkey[i] = -1;
         hval[2 * i] = 0ull;
         hval[2 * i + 1] = 0ull;
@@ -1097,14 +1113,14 @@ __global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_li
     const int cnt = *a.pcount;
     for (;;) {
         if (tid == 0) {
-            s_r = atomicAdd(w.ctl + 5, 1);
+            s_r = atomicAdd(w.ctl + H::ctl, 1);
             s_nu = 0;
         }
         __syncthreads();
         const int r = s_r;
         if (r >= cnt) break;
         const int e = w.rowE[r];
-        if (e == 0 || e > kWalkLightRowMax) {   // nothing found / taken by a whole CTA
+        if (e <= H::min_e || e > H::max_e || e == 0) {   // nothing found / another class
             __syncthreads();
             continue;
         }
@@ -1126,7 +1142,7 @@ __global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_li
                 if (!is_new) term = ff{-term.hi, -term.lo};
                 long long A, B;
                 fix_split(term, &A, &B);
-                int slot = (int)(((uint32_t)x * 2654435761u) >> 24) & (kLightHash - 1);
+                int slot = (int)(((uint32_t)x * 2654435761u) >> (32 - H::bits));
                 for (;;) {
                     const int old = atomicCAS(&hkey[slot], -1, x);
                     if (old == -1) {
@@ -1134,7 +1150,7 @@ __global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_li
                         break;
                     }
                     if (old == x) break;
-                    slot = (slot + 1) & (kLightHash - 1);
+                    slot = (slot + 1) & (H::hash - 1);
                 }
                 atomicAdd(&hval[2 * slot], (unsigned long long)A);
                 if (B) atomicAdd(&hval[2 * slot + 1], (unsigned long long)B);
@@ -1142,19 +1158,20 @@ __global__ void __launch_bounds__(kLightThreads, kLightCtasPerSm) k_walk_rows_li
         }
         __syncthreads();
         const int nu = s_nu;
-        for (int i = tid; i < nu; i += kLightThreads) {
+        for (int i = tid; i < nu; i += H::threads) {
             const int slot = hused[i];
             const int x = hkey[slot];
             const long long A0 = (long long)hval[2 * slot], B0 = (long long)hval[2 * slot + 1];
             hkey[slot] = -1;
             hval[2 * slot] = 0ull;
             hval[2 * slot + 1] = 0ull;
-            const ff v = fix_to_ff(A0 + (B0 >> 32), B0 & 0xFFFFFFFFll);
+            const long long A = A0 + (B0 >> 32), B = B0 & 0xFFFFFFFFll;   // 0 <= B < 2^32
+            const ff v = fix_to_ff(A, B);
             ff* p = a.Dl + rs + x;
             *p = ff_add(*p, v);
             unsigned long long* bp = reinterpret_cast<unsigned long long*>(a.bcfix + 2 * (size_t)x);
-            atomicAdd(bp, (unsigned long long)A0);
-            if (B0) atomicAdd(bp + 1, (unsigned long long)B0);
+            atomicAdd(bp, (unsigned long long)A);
+            if (B) atomicAdd(bp + 1, (unsigned long long)B);
         }
         __syncthreads();
     }
@@ -1180,7 +1197,10 @@ static void launch_walks(const Dev& d, const WalkUpd& upd, int nchunks, int vn) 
                    d.walk_acc2, d.walk_tl, d.walk_ctl, d.walk_rowE, d.stats, nchunks, upd};
     k_walk_units<DT><<<grid, kWalkThreads, walk_smem(d.n), d.st>>>(pair_args<DT>(d), w);
     k_walk_rows<DT><<<rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), d.st>>>(pair_args<DT>(d), w);
-    k_walk_rows_light<DT><<<d.nsm * kLightCtasPerSm, kLightThreads, 0, d.st>>>(pair_args<DT>(d), w);
+    k_walk_rows_hash<DT, WalkLight><<<d.nsm * WalkLight::ctas, WalkLight::threads, WalkLight::smem, d.st>>>(
+        pair_args<DT>(d), w);
+    k_walk_rows_hash<DT, WalkMid><<<d.nsm * WalkMid::ctas, WalkMid::threads, WalkMid::smem, d.st>>>(
+        pair_args<DT>(d), w);
     // the column test, which does nothing unless the walks' buffer overflowed
     PairArgs<DT> a = pair_args<DT>(d);
     a.gate = d.walk_ctl + 4;

@@ -98,6 +98,15 @@ def test_walk_long_paths_rows_for_whole_ctas():
     assert info["walk_pairs"] > 0 and info["walk_vertices"] > 0
 
 
+def test_walk_mid_size_rows():
+    # closing shorter unit paths into cycles: rows whose walks find between 129 and 1024
+    # vertices in all (the mid-size hash-table class) next to light and whole-CTA rows
+    for n in (24, 40, 64):
+        g = synth.path_graph(n, False, 1)
+        info = _walk_vs_test(g, [("edge", 0, n - 1, 1), ("edge", 3, n - 4, 2)], "i32", f"path {n} closed")
+        assert info["walk_vertices"] > 0
+
+
 def test_walk_long_stream():
     g = synth.barabasi_albert(400, 3, 1, 30, 8181)
     ups = synth.update_stream(g, 40, 40, 20, 8282, 1, 30, kmin=1, kmax=5)
