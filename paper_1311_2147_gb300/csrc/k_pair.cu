@@ -801,7 +801,7 @@ struct WalkArgs {
 constexpr int kWalkWarps = kWalkThreads / 32;
 constexpr int kWalkGrab = 1;         // units a warp takes at a time (unit costs vary too much for more)
 constexpr int kWalkLightRowMax = 128;   // rows whose walks found at most this many vertices: light CTAs
-constexpr int kWalkMidRowMax = 1024;    // up to this many: mid-size CTAs; more: k_walk_rows
+constexpr int kWalkMidRowMax = 512;     // up to this many: mid-size CTAs; more: k_walk_rows
 
 // d(s,x) of a state: the saved value where the pair changed in this update (old state).
 template <typename DT>
@@ -1076,8 +1076,8 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(P
 // memory (kHash slots, at least twice the vertices, so it never fills and every probe
 // ends), which is then added to delta_s and to BC's change and emptied.  Two classes:
 // light rows (at most 128 vertices; most rows, one to three changed targets) in 64-thread
-// CTAs, 32 per SM, and mid-size rows (129 to 1024 vertices) in 256-thread CTAs with a
-// 2048-slot table, 4 per SM.  Rows with more vertices go to k_walk_rows.
+// CTAs, 32 per SM, and mid-size rows (129 to 512 vertices) in 256-thread CTAs with a
+// 1024-slot table, 8 per SM.  Rows with more vertices go to k_walk_rows.
 template <int kThreads, int kCtas, int kHash, int kMinE, int kMaxE, int kCtl>
 struct WalkHash {
     static constexpr int threads = kThreads, ctas = kCtas, hash = kHash, min_e = kMinE, max_e = kMaxE, ctl = kCtl;
@@ -1089,7 +1089,7 @@ struct WalkHash {
                                    (size_t)kMaxE * sizeof(int32_t);
 };
 using WalkLight = WalkHash<64, 32, 256, 0, kWalkLightRowMax, 5>;
-using WalkMid = WalkHash<256, 4, 2048, kWalkLightRowMax, kWalkMidRowMax, 6>;
+using WalkMid = WalkHash<256, 8, 1024, kWalkLightRowMax, kWalkMidRowMax, 6>;
 static_assert(WalkMid::smem * WalkMid::ctas <= 200 * 1024, "mid-size tables fit the SM");
 static_assert(WalkMid::smem <= 48 * 1024 && WalkLight::smem <= 48 * 1024, "no opt-in shared memory needed");
 

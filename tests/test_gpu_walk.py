@@ -99,7 +99,7 @@ def test_walk_long_paths_rows_for_whole_ctas():
 
 
 def test_walk_mid_size_rows():
-    # closing shorter unit paths into cycles: rows whose walks find between 129 and 1024
+    # closing shorter unit paths into cycles: rows whose walks find between 129 and 512
     # vertices in all (the mid-size hash-table class) next to light and whole-CTA rows
     for n in (24, 40, 64):
         g = synth.path_graph(n, False, 1)
