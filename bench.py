@@ -321,7 +321,7 @@ def run_ours(args):
         kl = len(prof_updates)
         achieved = alg_bytes[dom] / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel_class": dom,
-                "kernel": "k_walk_units + k_walk_rows (DAG walks; with k_pair_plan, k_pair_weights)",
+                "kernel": "k_walk_units + k_walk_rows_hash + k_walk_rows (DAG walks; with k_pair_plan, k_pair_weights)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes[dom] / kl,
                 "traffic": read_traffic("walks_ba8192", (d_walk_arcs + d_walk_vtx) / kl),
