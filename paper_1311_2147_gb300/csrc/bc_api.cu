@@ -498,30 +498,38 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
         // rows with more changed targets than kPairCap (and row v): Algorithm 1 in full;
         // the others: pair corrections of their dependency rows
         timed(g, 4, 1, [&] { launch_pair_lists(d); });
+        // kernels of launch_pairdep: plan and weights, then the walks (units, two hash-table
+        // row classes, whole-CTA rows) and the gated column test, or the column test alone
+        const int pair_launches = walk ? 7 : 3;
         // BC: the full rows are subtracted before and added after their re-accumulation;
-        // the corrected rows add their changes to BC as they are made (k_pairdep)
-        timed(g, 2, 2, [&] { launch_bc_rows_list(d, -1, d.full_rows, d.counts + 3); });
+        // the corrected rows add their changes to BC's fixed-point change as they are
+        // made, which k_bc_fix folds into BC at the end
         if (!g->profile) {
             // the two write disjoint dependency rows and only read the rest of the state:
-            // the (latency-bound, often partial-wave) accumulation of the full rows runs
-            // on the second stream beside the pair corrections
+            // the full rows' BC sums and (latency-bound, often partial-wave)
+            // accumulation run on the second stream beside the pair corrections, which
+            // do not touch BC itself until k_bc_fix, after the join
             Dev ds = d;
             ds.st = g->side;
             CK(g, cudaEventRecord(g->ev_fork, d.st));
             CK(g, cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+            launch_bc_rows_list(ds, -1, d.full_rows, d.counts + 3);
             launch_accum_rows(ds, d.full_rows, d.counts + 3);
+            launch_bc_rows_list(ds, +1, d.full_rows, d.counts + 3);
             CK(g, cudaEventRecord(g->ev_join, g->side));
             launch_pairdep(d, walk ? &upd : nullptr);
             CK(g, cudaStreamWaitEvent(d.st, g->ev_join, 0));
-            g->launches += 4;
-        } else {
-            timed(g, 5, 3, [&] { launch_pairdep(d, walk ? &upd : nullptr); });
-            timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
-        }
-        timed(g, 2, 3, [&] {
-            launch_bc_rows_list(d, +1, d.full_rows, d.counts + 3);
             launch_bc_fix(d);
-        });
+            g->launches += 6 + pair_launches;
+        } else {
+            timed(g, 2, 2, [&] { launch_bc_rows_list(d, -1, d.full_rows, d.counts + 3); });
+            timed(g, 5, pair_launches, [&] { launch_pairdep(d, walk ? &upd : nullptr); });
+            timed(g, 1, 1, [&] { launch_accum_rows(d, d.full_rows, d.counts + 3); });
+            timed(g, 2, 3, [&] {
+                launch_bc_rows_list(d, +1, d.full_rows, d.counts + 3);
+                launch_bc_fix(d);
+            });
+        }
         timed(g, 4, 1, [&] { launch_pair_clear(d); });
     } else {
         timed(g, 4, 1, [&] { launch_compact(d, d.changed, 1, d.acc_rows, d.counts + 1, 0, 1); });
