@@ -120,6 +120,34 @@ def test_walk_buffer_overflow_falls_back_to_the_column_test():
     _walk_vs_test(g, ups, "i32", "walk buffer of 1 entry", cap=1)
 
 
+def test_row_lists_beyond_one_tile_of_flags():
+    # n = 16400 > 1024 threads x 16 flags: the changed-row and full-row lists (one pass
+    # over the flags, k_pair_lists) span two tiles.  Checked against a handle with the
+    # pair corrections off (every changed row re-accumulated, lists from k_compact) on
+    # BC and on rows of both tiles.
+    n = 16400
+    g = synth.erdos_renyi(n, 4 * n, 1, 50, 16400, directed=False)
+    ups = synth.update_stream(g, 2, 2, 2, 16401, 1, 50, kmin=2, kmax=6)
+    a = binding.BCGraph(g, dist="i32")
+    a.bc_set_option("pair_walk", 1)
+    b = binding.BCGraph(g, dist="i32")
+    b.bc_set_option("pair_updates", 0)
+    for h in (a, b):
+        rc, done = h.bc_apply_updates(ups)
+        assert rc == 0 and done == len(ups), h.last_error()
+    assert a.bc_get_info()["pair_rows"] > 0
+    for s0, cnt in ((0, 8), (16376, 24)):
+        da, sa, la = a.bc_get_rows(s0, cnt)
+        db, sb, lb = b.bc_get_rows(s0, cnt)
+        assert np.array_equal(da, db) and np.array_equal(sa, sb), f"rows {s0}..{s0 + cnt}"
+        ok, worst = close(la, lb)
+        assert ok, f"dependencies of rows {s0}..{s0 + cnt} differ ({worst:.3g} x tol)"
+    ok, worst = close(a.bc_get_scores(), b.bc_get_scores())
+    assert ok, f"BC differs ({worst:.3g} x tol)"
+    a.close()
+    b.close()
+
+
 def test_walk_option_rejected_on_directed_graphs():
     g = synth.erdos_renyi(20, 60, 1, 5, 3, directed=True)
     a = binding.BCGraph(g)
