@@ -180,17 +180,23 @@ struct PairArgs {
 // BC(x) += v for one corrected entry delta_s(x): v is added to the column's fixed-point
 // pair (A in units of 2^-24, B in units of 2^-56) by two integer atomics, so the total
 // does not depend on the order in which rows and CTAs add (the result is deterministic)
-// and is exact up to the 2^-57 rounding of each entry.  Bounds: each pair term
+// and is exact up to the 2^-56 rounding of each entry.  Bounds: each pair term
 // delta_st(x) lies in [0, 1] and a row has at most kPairCap targets, so |v| <= 128 and
 // |A| <= 2^31, |B| <= 2^31 per entry (the DAG walks add a row's column sum with
 // 0 <= B < 2^32); a column receives at most one entry per row, so for n < 2^20 both
 // sums stay below 2^52 and k_bc_fix converts them exactly.
 __device__ __forceinline__ void bc_fix_add(int64_t* fix, int x, ff v) {
-    const double vd = ((double)v.hi + (double)v.lo) * 0x1p24;   // exact
-    const double a = rint(vd);
-    const long long b = __double2ll_rn((vd - a) * 0x1p32);       // vd - a is exact, |.| <= 1/2
+    // in single precision, as fix_split: h = hi * 2^24 is exact (|h| <= 2^31) and so is
+    // h - rint(h); (h - a) * 2^32 and lo * 2^56 (|lo| <= 2^-17) are exact scalings, each
+    // rounded to an integer once, and a carry keeps |B| <= 2^31
+    const float h = v.hi * 0x1p24f;
+    const float a = rintf(h);
+    long long b = __float2ll_rn((h - a) * 0x1p32f) + __float2ll_rn(v.lo * 0x1p56f);
+    const long long c = (b + (1ll << 31)) >> 32;
+    const long long A = __float2ll_rn(a) + c;
+    b -= c << 32;
     unsigned long long* p = reinterpret_cast<unsigned long long*>(fix + 2 * (size_t)x);
-    atomicAdd(p, (unsigned long long)(long long)a);
+    atomicAdd(p, (unsigned long long)A);
     if (b) atomicAdd(p + 1, (unsigned long long)b);
 }
 
