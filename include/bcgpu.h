@@ -273,15 +273,17 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value);
  *   d_off        DEVICE int32[n+1]: CSR offsets by tail (arcs of a in [d_off[a], d_off[a+1])).
  *   d_dst, d_w   DEVICE int32 / int64 [arcs]: head and weight of each arc, weight in
  *                [1, INF-1] of the distance type.  An undirected graph is passed as
- *                G_D (both arcs of every edge).  The graph must be simple; a bad
- *                endpoint or weight found on the device returns BC_ERR_ARG.
+ *                G_D (both arcs of every edge).  The graph must be simple (repeated
+ *                arcs are the caller's to avoid); a bad endpoint, a self-loop or a bad
+ *                weight found on the device returns BC_ERR_ARG.
  *   flags        as for bc_init_static.
  *   d_scores     DEVICE double[n]: receives BC (halved G_D sums for undirected).
  *   cuda_stream  stream for all the work (NULL = legacy default stream).
- * Synchronous.  Calls no cudaMalloc / cudaFree and no allocating library routine.
- * The first call on a device looks up the device address of the scratch array
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  All calls share the one scratch array, which keeps the previous
+ * Synchronous: it waits for its stream and copies an error word to the host, so it
+ * must not be called while its stream (or the legacy stream) is being captured.
+ * Calls no cudaMalloc / cudaFree and no allocating library routine.  The first call on
+ * a device looks up the device address of the scratch array (cudaGetSymbolAddress)
+ * with that device current.  All calls share the one scratch array, which keeps the previous
  * call's contents (the call clears what must start at zero); calls whose work overlaps
  * on the GPU -- from several host threads or on several streams -- race on it.
  */

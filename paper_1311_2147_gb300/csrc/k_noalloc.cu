@@ -84,7 +84,10 @@ __global__ void k_pack_graph(int n, int64_t arcs, const int32_t* off, const int3
         len[i] = b - a;
         if (a < 0 || b < a || b > arcs) set_err(err, ERRF_ARG_DEVICE);
         else
-            for (int32_t e = a; e < b; ++e) src[e] = (int32_t)i;
+            for (int32_t e = a; e < b; ++e) {
+                src[e] = (int32_t)i;
+                if (dst[e] == (int32_t)i) set_err(err, ERRF_ARG_DEVICE);   // self-loop
+            }
     }
     if (i < arcs) {
         const int32_t b = dst[i];
