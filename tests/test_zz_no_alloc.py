@@ -87,11 +87,10 @@ def test_noalloc_second_call_allocates_nothing():
         g = make()
         rc, first = _call(lib, torch, g, flags)
         assert rc == binding.BC_OK
-        inputs = _device_inputs(torch, g)
+        t_off, t_dst, t_w, t_out = _device_inputs(torch, g)
+        stream = torch.cuda.current_stream().cuda_stream
         free0, _ = torch.cuda.mem_get_info()
         alloc0 = torch.cuda.memory_allocated()
-        stream = torch.cuda.current_stream().cuda_stream
-        t_off, t_dst, t_w, t_out = inputs
         rc = lib.bc_static_scores_noalloc(g.n, int(t_dst.shape[0]), t_off.data_ptr(), t_dst.data_ptr(),
                                           t_w.data_ptr(), flags, t_out.data_ptr(), stream)
         torch.cuda.synchronize()
