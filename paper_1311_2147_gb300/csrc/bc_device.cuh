@@ -247,6 +247,14 @@ struct ScanArgs {
     const uint64_t* cS;    // per column t: path count from v
     const uint64_t* cM;    // per column t: multiplier of a tie
     int skip_row;
+    // Ties with a zero tie multiplier add no paths (sigma += rowM * colM = 0), so for
+    // integer distances such a pair can change only if cand < d, i.e. cand + 1 <= d.
+    // tie_rows: rows with rowM = 0 take the quick test with rd + 1 (the IN phase, where
+    // every finite column has colM = sigma(v,t) > 0);  tie_cols: columns with colM = 0
+    // are staged as c + 1 (the OUT phase, where every finite row has rowM = sigma(s,v)
+    // > 0).  Never both in one pass: cand + 2 <= d would miss an improvement by one.
+    int tie_rows;
+    int tie_cols;
     int32_t* err;
     int64_t* stats;        // [4] pairs with a lower distance [5] pairs with new tied paths [6] rows
     PairRec rec;           // when rec.tcnt is set: record the changed pairs (pair corrections)
@@ -354,6 +362,123 @@ __device__ __forceinline__ bool rule_vec(const ScanArgs<DT>& a, int s, size_t ro
         }
     }
     return wr;
+}
+
+// VN consecutive path counts from a 16-byte aligned address, in 16-byte loads.
+template <int VN>
+__device__ __forceinline__ void load_u64s(const uint64_t* p, uint64_t* o) {
+#pragma unroll
+    for (int h = 0; h < VN / 2; ++h) {
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(p + 2 * h);
+        o[2 * h] = x.x;
+        o[2 * h + 1] = x.y;
+    }
+}
+
+// The rank-1 rule on a vector like rule_vec, recording nothing: returns the mask of
+// pairs q whose distance dropped (bits 0..7) or that gained paths at the same distance
+// (bits 8..15), with their values before the rule in dold / sold, for a caller that
+// records the changes of a whole warp together.  The vector's path counts and the
+// column's counts and multipliers are loaded together (16-byte loads: t is a multiple
+// of VN and so is n), and the changed counts written back together, so a vector costs
+// one round trip to memory instead of one per pair.
+template <typename DT>
+__device__ __forceinline__ unsigned rule_vec_masked(const ScanArgs<DT>& a, size_t rowoff, int t,
+                                                    typename Vec<DT>::T& dv, const typename Vec<DT>::T& cv,
+                                                    int64_t rd, uint64_t rs, uint64_t rm, int& n_changed,
+                                                    int& n_ties, int64_t* dold, uint64_t* sold) {
+    using V = Vec<DT>;
+    constexpr int VN = V::N;
+    const int64_t INF = Inf<DT>::v;
+    int64_t dd[VN], cd[VN];
+    uint64_t sg[VN], cs[VN], cm[VN];
+    V::unpack(dv, dd);
+    V::unpack(cv, cd);
+    load_u64s<VN>(a.S + rowoff + t, sg);
+    load_u64s<VN>(a.cS + t, cs);
+    load_u64s<VN>(a.cM + t, cm);
+    unsigned mask = 0;
+#pragma unroll
+    for (int q = 0; q < VN; ++q) {
+        dold[q] = dd[q];
+        sold[q] = sg[q];
+        if (cd[q] == INF) continue;
+        const int64_t cand = dsum<DT>(rd, cd[q]);
+        if (cand == SAT) {
+            if (dd[q] == INF) set_err(a.err, ERRF_DIST);
+            continue;
+        }
+        if (cand > dd[q]) continue;
+        if (cand < dd[q]) {
+            sg[q] = mul_chk(rs, cs[q], a.err);
+            V::set(dv, q, cand);
+            ++n_changed;
+            mask |= 1u << q;
+        } else {
+            const uint64_t p = mul_chk(rm, cm[q], a.err);
+            if (p != 0ull) {
+                sg[q] = add_chk(sg[q], p, a.err);
+                ++n_ties;
+                mask |= 1u << (q + 8);
+            }
+        }
+    }
+    if (mask) {
+#pragma unroll
+        for (int h = 0; h < VN / 2; ++h)
+            *reinterpret_cast<ulonglong2*>(a.S + rowoff + t + 2 * h) = make_ulonglong2(sg[2 * h], sg[2 * h + 1]);
+    }
+    return mask;
+}
+
+// Records, for the whole warp, the changes one rule_vec_masked per lane found: lane
+// holds row s (s < 0: nothing), the vector's first column t (a multiple of VN, so its
+// pairs share one change-map word) and the changed pairs in bits; lanes with the same
+// row must be consecutive.  One change-map OR per lane and one target-count atomic per
+// run of lanes on the same row; the first change of a pair in the update saves its old
+// values and lists it, as record_change does.  Every lane of the warp must call it.
+template <typename DT>
+__device__ __forceinline__ void record_changes_warp(const PairRec& r, int n, int s, int t, unsigned bits,
+                                                    const int64_t* dold, const uint64_t* sold) {
+    const int lane = threadIdx.x & 31;
+    if (s >= 0 && bits) {
+        uint32_t* w = r.chg + (size_t)s * r.chg_words + (t >> 5);
+        unsigned wb = bits << (t & 31);
+        if (!r.first) wb &= ~*w;   // pairs already recorded in this update keep their saved values
+        bits = wb >> (t & 31);
+        if (wb) atomicOr(w, wb);
+        const size_t i0 = (size_t)s * n + t;
+        for (unsigned b = bits; b; b &= b - 1) {
+            const int q = __ffs(b) - 1;
+            static_cast<DT*>(r.oldD)[i0 + q] = (DT)dold[q];
+            r.oldS[i0 + q] = sold[q];
+        }
+    } else {
+        bits = 0;
+    }
+    // segmented scan of the counts over runs of lanes with the same row
+    const int c = __popc(bits);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int s_prev = __shfl_up_sync(0xffffffffu, s, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || s_prev != s);
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int start = 31 - __clz(starts & upto);
+    const unsigned after = starts & ~upto;
+    const int end = after ? __ffs(after) - 2 : 31;
+    const int before = __shfl_sync(0xffffffffu, incl, start > 0 ? start - 1 : 0);
+    const int base_incl = start > 0 ? before : 0;
+    const int total = __shfl_sync(0xffffffffu, incl, end) - base_incl;
+    int base = 0;
+    if (lane == start && s >= 0 && total > 0) base = atomicAdd(r.tcnt + s, total);
+    base = __shfl_sync(0xffffffffu, base, start);
+    int pos = base + (incl - c - base_incl);
+    for (unsigned b = bits; b; b &= b - 1, ++pos)
+        if (pos < r.tcap) r.tlist[(size_t)s * r.tcap + pos] = t + __ffs(b) - 1;
 }
 
 template <typename DT>

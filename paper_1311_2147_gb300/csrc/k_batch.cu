@@ -174,6 +174,8 @@ __device__ __forceinline__ ScanArgs<DT> batch_scan_args(const Dev& d, const Batc
     a.fM = d.fM;
     a.err = d.err;
     a.stats = d.stats;
+    a.tie_rows = 0;
+    a.tie_cols = 0;
     a.rec = PairRec{};   // the batched path re-accumulates every changed row
     if (phase == 0) {
         a.cD = (const DT*)d.D + (size_t)u.v * d.n;

@@ -126,126 +126,221 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
     scan_stats(a.stats, n_changed, n_ties);
 }
 
-// Row v <- the OUT phase's result; with rec.tcnt set, the pairs (v,t) whose distance or
-// path count changes are recorded.
-// K2, vector path (n a multiple of the vector width).  Work item = (chunk c of CW
-// columns, row i) in chunk-major order, so the column vector of a chunk is staged in
-// shared memory (with its largest finite value) once for all the rows a CTA meets in
-// that chunk; CTAs take items in turn.  Each thread issues the kScanVecs 16-byte loads
-// of its part of the row chunk before using any (the row of the next item is fetched a
-// step ahead, so these loads do not wait for it), then applies the quick test of the
-// rule to every vector and the rule itself (scan_vec) to the rare vectors that can
-// change.  Changed vectors are written back to D.  (Measured alternatives: a bulk-copy
-// (TMA) pipeline with 2-6 stages of 16 KB per CTA and a contiguous block of items per
-// CTA were both slower on this pass.)
-constexpr int kScanVecs = 8;
-constexpr int kScanCtasPerSm = 4;
+// K2, vector path (n a multiple of the vector width): column-stationary CTAs.  CTA b
+// owns column chunk c = b mod nch (kCsThreads threads x kCsVpt 16-byte vectors) for
+// the whole launch and walks the rows i = b / nch, + gridDim / nch, ... of the list.
+// Its column values -- with the tie_cols bump, for the quick test -- sit in registers,
+// loaded once; each thread streams its part of every row through a ring of kCsStages
+// rows in shared memory filled by cp.async (16-byte copies that hold no registers
+// while in flight, and that only the issuing thread reads back, so no CTA barrier is
+// needed in the loop).  The rule itself runs only for the rare vectors that pass the
+// quick test, with the true column values read from L2.  Changed vectors are written
+// to D directly.
+constexpr int kCsThreads = 256;
+constexpr int kCsVpt = 4;
+constexpr int kCsStages = 4;
+constexpr int kCsCtasPerSm = 3;
+constexpr size_t kCsRingBytes = (size_t)kCsStages * kCsVpt * kCsThreads * 16;
 
-template <typename DT>
-__global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm) k_scan_cm(ScanArgs<DT> a) {
+__device__ __forceinline__ void cs_copy16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global.L2::128B [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cs_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cs_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cs_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// WHOLE: n is a multiple of the chunk width, so no column of a chunk lies past n.
+template <typename DT, bool WHOLE>
+__global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<DT> a, int nch) {
     using V = Vec<DT>;
+    using VT = typename V::T;
     constexpr int VN = V::N;
-    constexpr int CW = kScanThreads * VN * kScanVecs;
-    extern __shared__ __align__(16) unsigned char smem[];
-    DT* scd = reinterpret_cast<DT*>(smem);   // CW column values
+    constexpr int CW = kCsThreads * kCsVpt * VN;
+    constexpr int ST = kCsStages;
+    extern __shared__ __align__(16) unsigned char cs_smem[];
+    VT (*stage)[kCsVpt][kCsThreads] = reinterpret_cast<VT (*)[kCsVpt][kCsThreads]>(cs_smem);
+    __shared__ unsigned long long s_cmax;
     if (block_err(a.err)) return;
     const int tid = threadIdx.x;
     const int n = a.n;
     const int64_t INF = Inf<DT>::v;
     const int cnt = *a.count;
-    const int nchunks = (n + CW - 1) / CW;
-    const int total = cnt * nchunks;   // at most 32768 rows x 16 chunks
+    const int gpc = (int)gridDim.x / nch;   // CTAs per column chunk
+    const int c = (int)blockIdx.x % nch;
+    const int r0 = (int)blockIdx.x / nch;
     if (blockIdx.x == 0 && tid == 0)
         atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6), (unsigned long long)cnt);
-    int n_changed = 0, n_ties = 0;
-    {
-        // CTAs take items in turn (item = block + k * grid): at any moment the CTAs
-        // read neighbouring rows, which keeps the DRAM accesses of the whole grid local
-        __shared__ int64_t s_cmax;
-        int64_t cmax = 0;
-        int cur_c = -1;
-        int item = blockIdx.x;
-        // the row of an item is fetched two items ahead and its distance to v one item
-        // ahead, so neither the loads of D nor the distance load wait for a load issued
-        // in the same item
-        auto rd_of = [&](int r) { return (r == a.skip_row) ? INF : (int64_t)a.fD[r]; };
-        auto row_of = [&](int it) { return it < total ? a.rows[it - (it / cnt) * cnt] : 0; };
-        int s_next = row_of(item);
-        int64_t rd_next = item < total ? rd_of(s_next) : INF;
-        int s_next2 = row_of(item + (int)gridDim.x);
-        for (; item < total; item += gridDim.x) {
-            const int c = item / cnt;
-            const int t0 = c * CW;
-            const int s = s_next;
-            const int64_t rd = rd_next;
-            if (item + (int)gridDim.x < total) {
-                s_next = s_next2;
-                rd_next = rd_of(s_next);
-                s_next2 = row_of(item + 2 * (int)gridDim.x);
+    if (r0 >= gpc || r0 >= cnt) return;   // block-uniform: no rows for this CTA
+    const int t0 = c * CW;
+    // the column chunk: quick-test values in registers; cmax = largest finite TRUE value
+    // (the bound that makes the one-compare quick test overflow-free)
+    VT cq[kCsVpt];
+    int64_t m = 0;
+#pragma unroll
+    for (int u = 0; u < kCsVpt; ++u) {
+        const int t = t0 + (u * kCsThreads + tid) * VN;
+        if (WHOLE || t < n) {
+            VT x = __ldg(reinterpret_cast<const VT*>(a.cD + t));
+            int64_t xv[VN];
+            V::unpack(x, xv);
+#pragma unroll
+            for (int q = 0; q < VN; ++q) {
+                if (xv[q] != INF && xv[q] > m) m = xv[q];
+                if (a.tie_cols && xv[q] < INF - 1 && __ldg(a.cM + t + q) == 0ull) V::set(x, q, xv[q] + 1);
             }
-            if (c != cur_c) {   // block-uniform: stage the column chunk and its largest finite value
-                cur_c = c;
-                __syncthreads();   // the previous chunk is no longer read
-                if (tid == 0) s_cmax = 0;
-                __syncthreads();
-                int64_t m = 0;
-#pragma unroll
-                for (int u = 0; u < kScanVecs; ++u) {
-                    const int j = (u * kScanThreads + tid) * VN;
-                    if (t0 + j < n) {
-                        const typename V::T x = __ldg(reinterpret_cast<const typename V::T*>(a.cD + t0 + j));
-                        *reinterpret_cast<typename V::T*>(scd + j) = x;
-                        int64_t xv[VN];
-                        V::unpack(x, xv);
-#pragma unroll
-                        for (int q = 0; q < VN; ++q)
-                            if (xv[q] != INF && xv[q] > m) m = xv[q];
-                    }
-                }
-                atomicMax(reinterpret_cast<unsigned long long*>(&s_cmax), (unsigned long long)m);
-                __syncthreads();
-                cmax = s_cmax;
-            }
-            if (rd != INF) {
-                const size_t rowoff = (size_t)s * n;
-                DT* Drow = a.D + rowoff;
-                typename V::T dv[kScanVecs];
-#pragma unroll
-                for (int u = 0; u < kScanVecs; ++u) {
-                    const int t = t0 + (u * kScanThreads + tid) * VN;
-                    if (t < n) dv[u] = __ldcs(reinterpret_cast<const typename V::T*>(Drow + t));
-                }
-                // quick test of every vector first; the rare vectors that can change are
-                // read again (from cache) by a loop that is not unrolled, so the rule's
-                // code does not hold the registers of all kScanVecs vectors.  When no
-                // finite sum of the row can exceed a finite distance bound (rd + the
-                // chunk's largest finite column value < INF), the test is one add and
-                // compare per pair.
-                const bool small = rd + cmax < INF;
-                unsigned cand = 0;
-#pragma unroll
-                for (int u = 0; u < kScanVecs; ++u) {
-                    const int j = (u * kScanThreads + tid) * VN;
-                    if (t0 + j >= n) break;
-                    const typename V::T cv = *reinterpret_cast<const typename V::T*>(scd + j);
-                    if (quick_vec<DT>(dv[u], cv, rd, small)) cand |= 1u << u;
-                }
-                if (cand) {
-                    const uint64_t rs = a.fS[s], rm = a.fM[s];
-                    while (cand) {
-                        const int u = __ffs(cand) - 1;
-                        cand &= cand - 1;
-                        const int j = (u * kScanThreads + tid) * VN;
-                        const int t = t0 + j;
-                        typename V::T d1 = *reinterpret_cast<const typename V::T*>(Drow + t);
-                        const typename V::T cv = *reinterpret_cast<const typename V::T*>(scd + j);
-                        if (rule_vec<DT>(a, s, rowoff, t, d1, cv, rd, rs, rm, n_changed, n_ties))
-                            *reinterpret_cast<typename V::T*>(Drow + t) = d1;
-                    }
-                }
-            }
+            cq[u] = x;
         }
     }
+    if (tid == 0) s_cmax = 0ull;
+    __syncthreads();
+    atomicMax(&s_cmax, (unsigned long long)m);
+    __syncthreads();
+    const int64_t cmax = (int64_t)s_cmax;
+    // rows i_k = r0 + k * gpc of the list, k = 0 .. nk-1, ST of them in flight
+    const int nk = (cnt - r0 + gpc - 1) / gpc;
+    int n_changed = 0, n_ties = 0;
+    // Row ids and per-row scalars come in batches of 32: lane j of every warp holds row
+    // k0 + j of the current batch and of the next one (loaded a whole batch ahead, so
+    // the issue never waits for them), and the issue takes its row's values by shuffle.
+    // Per stage: the row it holds and that row's scalars (consumed ST rows later).
+    const int lane = tid & 31;
+    auto batch_row = [&](int k) { return k < nk ? a.rows[r0 + k * gpc] : -1; };
+    int cur_s = batch_row(lane), nxt_s = batch_row(32 + lane);
+    DT cur_d = cur_s >= 0 ? a.fD[cur_s] : (DT)0;
+    DT nxt_d = nxt_s >= 0 ? a.fD[nxt_s] : (DT)0;
+    unsigned long long cur_m = (a.tie_rows && cur_s >= 0) ? a.fM[cur_s] : 1ull;
+    unsigned long long nxt_m = (a.tie_rows && nxt_s >= 0) ? a.fM[nxt_s] : 1ull;
+    int ring_s[ST];
+    DT ring_d[ST];
+    unsigned long long ring_m[ST];
+    int k_issue = 0;
+    auto issue = [&](int st) {
+        const int j = k_issue & 31;
+        if (j == 0 && k_issue > 0) {   // CTA-uniform: move to the next batch, fetch the one after
+            cur_s = nxt_s;
+            cur_d = nxt_d;
+            cur_m = nxt_m;
+            nxt_s = batch_row(k_issue + 32 + lane);
+            nxt_d = nxt_s >= 0 ? a.fD[nxt_s] : (DT)0;
+            nxt_m = (a.tie_rows && nxt_s >= 0) ? a.fM[nxt_s] : 1ull;
+        }
+        const int s = __shfl_sync(0xffffffffu, cur_s, j);
+        ring_s[st] = s;
+        ring_d[st] = __shfl_sync(0xffffffffu, cur_d, j);
+        ring_m[st] = __shfl_sync(0xffffffffu, cur_m, j);
+        if (s >= 0) {
+            const DT* src = a.D + (size_t)s * n;
+#pragma unroll
+            for (int u = 0; u < kCsVpt; ++u) {
+                const int t = t0 + (u * kCsThreads + tid) * VN;
+                if (WHOLE || t < n) cs_copy16(&stage[st][u][tid], src + t);
+            }
+        }
+        cs_commit();
+        ++k_issue;
+    };
+    // Candidate vectors (s, t) of this warp, waiting for the rule: applying it takes a
+    // few dependent memory round trips, which the 32 lanes then take together instead
+    // of one candidate at a time while the warp's row stream waits.
+    int2* wq = reinterpret_cast<int2*>(cs_smem + kCsRingBytes) + (tid >> 5) * 64;
+    int qn = 0;   // warp-uniform
+    auto run_queued = [&](int count) {
+        int s = -1, t = 0;
+        unsigned bits = 0;
+        int64_t dold[VN];
+        uint64_t sold[VN];
+        if (lane < count) {
+            const int2 e = wq[lane];
+            s = e.x;
+            t = e.y;
+            const size_t rowoff = (size_t)s * n;
+            const int64_t rd = (int64_t)a.fD[s];
+            const uint64_t rs = a.fS[s], rm = a.fM[s];
+            VT dv = *reinterpret_cast<const VT*>(a.D + rowoff + t);
+            const VT cv = __ldg(reinterpret_cast<const VT*>(a.cD + t));
+            const unsigned m = rule_vec_masked<DT>(a, rowoff, t, dv, cv, rd, rs, rm, n_changed, n_ties, dold, sold);
+            if (m & 0xffu) *reinterpret_cast<VT*>(a.D + rowoff + t) = dv;
+            bits = (m | (m >> 8)) & 0xffu;
+        }
+        if (a.rec.tcnt) record_changes_warp<DT>(a.rec, n, s, t, bits, dold, sold);
+    };
+#pragma unroll
+    for (int st = 0; st < ST; ++st) issue(st);
+    for (int kb = 0; kb < nk; kb += ST) {
+#pragma unroll
+        for (int st = 0; st < ST; ++st) {
+            if (kb + st >= nk) break;
+            cs_wait<ST - 1>();
+            const int s = ring_s[st];
+            const int64_t rd = (s == a.skip_row) ? INF : (int64_t)ring_d[st];
+            // the quick test's row term: rd + 1 where no tie of the row can add paths
+            const int64_t rq = (rd < INF - 1 && ring_m[st] == 0ull) ? rd + 1 : rd;
+            if (rd != INF) {
+                const bool small = rd + cmax < INF;
+                unsigned cand = 0;
+                if (small) {
+                    // no finite sum of the row reaches INF: a pair can change only if
+                    // d - c >= rq, so one max over the thread's pairs decides whether
+                    // any vector needs the per-vector test (d, c in [0, INF]: the
+                    // differences fit DT)
+                    DT mx = (DT)-Inf<DT>::v;
+#pragma unroll
+                    for (int u = 0; u < kCsVpt; ++u) {
+                        const int t = t0 + (u * kCsThreads + tid) * VN;
+                        if (WHOLE || t < n) {
+                            const VT x = stage[st][u][tid];
+                            const DT* xd = reinterpret_cast<const DT*>(&x);
+                            const DT* cd = reinterpret_cast<const DT*>(&cq[u]);
+#pragma unroll
+                            for (int q = 0; q < VN; ++q) mx = max(mx, (DT)(xd[q] - cd[q]));
+                        }
+                    }
+                    if ((int64_t)mx >= rq) {
+#pragma unroll
+                        for (int u = 0; u < kCsVpt; ++u) {
+                            const int t = t0 + (u * kCsThreads + tid) * VN;
+                            if ((WHOLE || t < n) && quick_vec<DT>(stage[st][u][tid], cq[u], rq, true)) cand |= 1u << u;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kCsVpt; ++u) {
+                        const int t = t0 + (u * kCsThreads + tid) * VN;
+                        if ((WHOLE || t < n) && quick_vec<DT>(stage[st][u][tid], cq[u], rq, false)) cand |= 1u << u;
+                    }
+                }
+                // candidates go to the warp's queue; the rule runs 32 at a time
+                if (__any_sync(0xffffffffu, cand != 0u)) {
+#pragma unroll
+                    for (int u = 0; u < kCsVpt; ++u) {
+                        const bool mine = (cand >> u) & 1u;
+                        const unsigned b = __ballot_sync(0xffffffffu, mine);
+                        if (!b) continue;
+                        if (mine)
+                            wq[qn + __popc(b & ((1u << lane) - 1u))] =
+                                make_int2(s, t0 + (u * kCsThreads + tid) * VN);
+                        qn += __popc(b);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            run_queued(32);
+                            __syncwarp();
+                            if (lane < qn - 32) wq[lane] = wq[32 + lane];
+                            qn -= 32;
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+            // refill the stage just read with the row ST ahead (this thread's reads of
+            // it are complete: their values were used above)
+            issue(st);
+        }
+    }
+    cs_wait_all();
+    __syncwarp();
+    run_queued(qn);
     scan_stats(a.stats, n_changed, n_ties);
 }
 
@@ -329,19 +424,20 @@ void launch_compact(const Dev& d, const uint8_t* mark, int clear, int32_t* rows,
                                                full, stats ? d.stats : nullptr, d.err);
 }
 
-// Dynamic shared memory of k_scan_cm: one chunk of the column vector.
-template <typename DT>
-static constexpr size_t scan_cm_smem() {
-    return (size_t)kScanThreads * Vec<DT>::N * kScanVecs * sizeof(DT);
-}
+// Dynamic shared memory of k_scan_cs: its ring of kCsStages row chunks, then a queue
+// of 64 candidate vectors per warp.
+constexpr size_t kCsSmem = kCsRingBytes + (size_t)(kCsThreads / 32) * 64 * sizeof(int2);
 
 // Allows the vector-path kernels their shared memory on the current device.
 cudaError_t scan_setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_scan_cm<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)scan_cm_smem<int32_t>());
+    const int b = (int)kCsSmem;
+    cudaError_t e = cudaFuncSetAttribute(k_scan_cs<int32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_scan_cm<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)scan_cm_smem<int64_t>());
+        e = cudaFuncSetAttribute(k_scan_cs<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scan_cs<int64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scan_cs<int64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return e;
 }
 
@@ -349,7 +445,13 @@ template <typename DT>
 static void scan_dispatch(const Dev& d, ScanArgs<DT> a) {
     constexpr int VN = Vec<DT>::N;
     if (d.n % VN == 0) {
-        k_scan_cm<DT><<<d.nsm * kScanCtasPerSm, kScanThreads, scan_cm_smem<DT>(), d.st>>>(a);
+        constexpr int CW = kCsThreads * kCsVpt * VN;
+        const int nch = (d.n + CW - 1) / CW;
+        const int per = std::max(1, d.nsm * kCsCtasPerSm / nch);
+        if (d.n % CW == 0)
+            k_scan_cs<DT, true><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+        else
+            k_scan_cs<DT, false><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
     } else {
         k_scan<DT, false><<<d.nsm * 8, kScanThreads, 0, d.st>>>(a);
     }
@@ -367,6 +469,8 @@ static ScanArgs<DT> scan_args(const Dev& d) {
     a.fS = d.fS;
     a.fM = d.fM;
     a.skip_row = -1;
+    a.tie_rows = 0;
+    a.tie_cols = 0;
     a.err = d.err;
     a.stats = d.stats;
     a.rec = d.pair_on ? pair_rec(d) : PairRec{};
@@ -379,6 +483,7 @@ void launch_scan_in(const Dev& d, int32_t v) {
     if (d.dbytes == 4) {
         ScanArgs<int32_t> a = scan_args<int32_t>(d);
         a.rec.first = 1;
+        a.tie_rows = 1;
         a.cD = (const int32_t*)d.D + (size_t)v * d.n;
         a.cS = d.S + (size_t)v * d.n;
         a.cM = a.cS;
@@ -386,6 +491,7 @@ void launch_scan_in(const Dev& d, int32_t v) {
     } else {
         ScanArgs<int64_t> a = scan_args<int64_t>(d);
         a.rec.first = 1;
+        a.tie_rows = 1;
         a.cD = (const int64_t*)d.D + (size_t)v * d.n;
         a.cS = d.S + (size_t)v * d.n;
         a.cM = a.cS;
@@ -402,6 +508,7 @@ void launch_scan_out(const Dev& d, int32_t v) {
         a.cS = d.cS;
         a.cM = d.cM;
         a.skip_row = v;
+        a.tie_cols = 1;
         scan_dispatch<int32_t>(d, a);
     } else {
         ScanArgs<int64_t> a = scan_args<int64_t>(d);
@@ -409,6 +516,7 @@ void launch_scan_out(const Dev& d, int32_t v) {
         a.cS = d.cS;
         a.cM = d.cM;
         a.skip_row = v;
+        a.tie_cols = 1;
         scan_dispatch<int64_t>(d, a);
     }
 }
