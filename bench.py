@@ -254,6 +254,24 @@ def extend_stream(name: str, g, ups, extra: int, seed: int):
     return list(ups) + more
 
 
+def per_class_rates(dev_ms, kinds):
+    """Per-update device times split by class: edge / vertex updates, and no-ops (an
+    update that changes no pair) against effective ones.  Each class: count, rate
+    (updates per second of its own device time), mean and p50/p99 of the device time."""
+    out = {}
+    groups = {"edge": [], "vertex": [], "noop": [], "effective": [], "all": []}
+    for ms, (kind, noop) in zip(dev_ms, kinds):
+        groups[kind].append(ms)
+        groups["noop" if noop else "effective"].append(ms)
+        groups["all"].append(ms)
+    for k, v in groups.items():
+        if not v:
+            continue
+        out[k] = {"count": len(v), "updates_per_s": 1e3 * len(v) / sum(v), "mean_ms": float(np.mean(v)),
+                  "p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+    return out
+
+
 def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
     """The largest x over all ranks of the process group (x itself on one process)."""
     if dist is None:
@@ -401,28 +419,42 @@ def run_ours(args):
         A.bc_set_option("full_scan", 1)
         A.bc_set_option("profile", 1)
         A.bc_get_profile(reset=True)
-        i0 = A.bc_get_info()
-        rc, _ = A.bc_apply_updates(extra)
-        assert rc == 0, A.last_error()
-        pf = A.bc_get_profile(reset=True)
-        i1 = A.bc_get_info()
+        tot_ms = tot_b = 0.0
+        tot_nl = tot_rows = 0
+        per_upd = []
+        for up in extra:   # one update at a time: per-update figures beside the totals
+            i0 = A.bc_get_info()
+            rc, _ = A.bc_apply_updates([up])
+            assert rc == 0, A.last_error()
+            pf = A.bc_get_profile(reset=True)
+            i1 = A.bc_get_info()
+            ms, nl = pf["scan"]
+            rows = i1["rows_scanned"] - i0["rows_scanned"]
+            low, tie = i1["pairs_lowered"] - i0["pairs_lowered"], i1["pairs_tied"] - i0["pairs_tied"]
+            b = rows * n * sd + tie * 16 + low * (sd + 8)
+            if nl:
+                per_upd.append({"kind": up[0], "launches": nl, "avg_launch_ms": ms / nl,
+                                "gbs": b / (ms / 1e3) / 1e9, "pairs_changed": low + tie})
+            tot_ms += ms
+            tot_b += b
+            tot_nl += nl
+            tot_rows += rows
         A.bc_set_option("profile", 0)
         A.bc_set_option("full_scan", 0)
-        ms, nl = pf["scan"]
-        rows = i1["rows_scanned"] - i0["rows_scanned"]
-        b = rows * n * sd + (i1["pairs_tied"] - i0["pairs_tied"]) * 16 + \
-            (i1["pairs_lowered"] - i0["pairs_lowered"]) * (sd + 8)
-        if ms > 0 and nl > 0:
-            achieved = b / (ms / 1e3) / 1e9
-            roof_scan = {"bound": "hbm", "kernel": "k_scan_cm, every row (full pass)", "achieved": achieved,
+        if tot_ms > 0 and tot_nl > 0:
+            achieved = tot_b / (tot_ms / 1e3) / 1e9
+            roof_scan = {"bound": "hbm", "kernel": "k_scan_cs, every row (full pass)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": b / nl,
-                         "traffic": read_traffic("scan_ba8192_fullscan", rows * n / nl),
-                         "launches": nl, "avg_launch_ms": ms / nl, "updates": len(extra)}
+                         "alg_bytes_per_launch": tot_b / tot_nl,
+                         "traffic": read_traffic("scan_ba8192_fullscan", tot_rows * n / tot_nl),
+                         "launches": tot_nl, "avg_launch_ms": tot_ms / tot_nl, "updates": len(extra),
+                         "median_update_gbs": float(np.median([u["gbs"] for u in per_upd])),
+                         "per_update": per_upd}
     A.close()
 
     # ---------------- e2e through the C-ABI with host buffers, per-update latency
     e2e = None
+    per_class = None
     lat = []
     if not args.no_e2e:
         B = binding.BCGraph(g, dist=dtype, stream=stream.cuda_stream)
@@ -432,24 +464,65 @@ def run_ours(args):
         barrier()
         h2d = 0
         d2h = 0
+        # device time of every update (events on the library's stream around its call)
+        # and its class, for the per-class rates
+        evs = []
+        kinds = []
         t0 = time.perf_counter()
         for s in sl[W:W + K]:
             for up in s:
                 rec, ed = binding.encode_updates([up])
                 h2d += rec.nbytes + ed.nbytes
                 d2h += 4
+                ea = torch.cuda.Event(enable_timing=True)
+                eb = torch.cuda.Event(enable_timing=True)
+                noop0 = B.bc_get_info()["noop_updates"]
                 ta = time.perf_counter()
+                ea.record(stream)
                 rc, _ = B.bc_apply_updates((rec, ed))
+                eb.record(stream)
                 lat.append(1e3 * (time.perf_counter() - ta))
                 assert rc == 0, B.last_error()
+                evs.append((ea, eb))
+                kinds.append((up[0], B.bc_get_info()["noop_updates"] > noop0))
             scores = B.bc_get_scores()
             d2h += 2 * scores.nbytes
         barrier()
         wall = max_over_ranks(time.perf_counter() - t0, dist)
+        dev = [ea.elapsed_time(eb) for ea, eb in evs]
         e2e = {"value": job_rate(len(timed), world, wall), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                "d2h_bytes_per_step": d2h // K, "p50_ms": float(np.percentile(lat, 50)),
                "p99_ms": float(np.percentile(lat, 99))}
+        per_class = per_class_rates(dev, kinds)
         B.close()
+
+    # ---------------- complete graph: the "effective decreases" variant (w' <= d(u,v),
+    # d read from the handle's own state through the C-ABI), per-update device times
+    effective = None
+    if args.workload == "complete2048" and not args.no_e2e:
+        C = binding.BCGraph(g, dist=dtype, stream=stream.cuda_stream)
+        rows = {}
+
+        def dist_uv(a_, b_):
+            if a_ not in rows:
+                rows[a_] = C.bc_get_rows(int(a_), 1, want=("d",))[0][0]
+            return int(rows[a_][b_])
+        dec = synth.effective_decreases(g, dist_uv, args.effective_updates, 0xEFFE)
+        devs, kinds = [], []
+        for up in dec:
+            ea = torch.cuda.Event(enable_timing=True)
+            eb = torch.cuda.Event(enable_timing=True)
+            noop0 = C.bc_get_info()["noop_updates"]
+            ea.record(stream)
+            rc, _ = C.bc_apply_updates([up])
+            eb.record(stream)
+            assert rc == 0, C.last_error()
+            kinds.append((up[0], C.bc_get_info()["noop_updates"] > noop0))
+            devs.append((ea, eb))
+        torch.cuda.synchronize()
+        effective = {"updates": len(dec), "draw": "w' ~ U[1, min(w-1, d(u,v))] on random existing arcs",
+                     "per_class": per_class_rates([a_.elapsed_time(b_) for a_, b_ in devs], kinds)}
+        C.close()
 
     # ---------------- baselines: GPU full recompute and the CPU oracle (rank 0 only)
     gpu_full = None
@@ -493,7 +566,8 @@ def run_ours(args):
                 "clocks": clk.summary(), "gpu_full_recompute": gpu_full,
                 "latency_ms": {"p50": e2e["p50_ms"], "p99": e2e["p99_ms"]} if e2e else None,
                 "roofline_scan": roof_scan,
-                "classes": classes, "rows_per_update": rows_per_upd, "per_update": per_update}
+                "classes": classes, "rows_per_update": rows_per_upd, "per_update": per_update,
+                "per_class": per_class, "effective_decreases": effective}
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -516,6 +590,8 @@ def run_batch(args):
     fam = synth.workload_batch(count=args.batch_graphs, n_updates=per, rounds=total_steps)
     gen_s = time.perf_counter() - t0
     graphs = [binding.BCGraph(g, dist="i32") for g, _ in fam]
+    # baseline: one static recompute (bc_init_static) of every graph per update it takes
+    init_ms = [h.bc_get_info()["last_init_ms"] for h in graphs]
     stream = torch.cuda.Stream()
     batch = binding.BCBatch(graphs, stream=stream.cuda_stream)
     step_i = [0]
@@ -549,6 +625,11 @@ def run_batch(args):
                                    f"8 edge updates per graph per step",
                        "sum_n2": sum_n2, "state_gb": sum_n2 * 20 / 1e9, "tiles": tiles,
                        "autotune_trials": trials, "generation_s": gen_s},
+            "gpu_full_recompute": {"sum_init_ms": sum(init_ms), "updates_per_s": len(fam) / (sum(init_ms) / 1e3),
+                                   "note": "bc_init_static of every graph once per update of that graph "
+                                           "(the sum of the per-graph static times at creation)",
+                                   "incremental_speedup": (updates / (total_ms / 1e3)) /
+                                                          (len(fam) / (sum(init_ms) / 1e3))},
             "clocks": clk.summary()}
     print(json.dumps(line))
     return 0
@@ -574,8 +655,10 @@ def run_serve(args):
              else synth.barabasi_albert(n, 8, 1, 100, synth.sub_seed(seed, i)))
         graphs.append(g)
     R = args.serve_requests
-    # requests over uniformly drawn graphs, each stream valid against its own graph
-    pick = rng.below(G, 2 * R + 64).tolist()
+    loads = [float(x) for x in str(args.serve_loads).split(",")] if args.serve_loads else [args.serve_load]
+    # requests over uniformly drawn graphs, each stream valid against its own graph:
+    # R closed-loop requests, then R open-loop requests per load
+    pick = rng.below(G, (1 + len(loads)) * R + 64).tolist()
     per_graph = [0] * G
     for gi in pick:
         per_graph[gi] += 1
@@ -593,7 +676,7 @@ def run_serve(args):
     state = sum(n * n * 20 for n in ns)
     srv = binding.BCServer(budget_bytes=int(state * 1.5) + (8 << 30), max_batch=64)
     gids = [srv.add_graph(g) for g in graphs]
-    # closed loop: saturated throughput on the first half
+    # closed loop: saturated throughput on the first R requests
     closed = seq[:R]
     t0 = time.perf_counter()
     for gi, up in closed:
@@ -601,40 +684,48 @@ def run_serve(args):
     res_c = srv.drain()
     t_closed = time.perf_counter() - t0
     sat = len(closed) / t_closed
-    # open loop: Poisson arrivals at load x saturated throughput on the second half
-    lam = args.serve_load * sat
-    gaps = -np.log(1.0 - synth.Rng(seed + 1).unit(R)) / lam
-    arrivals = np.cumsum(gaps)
-    opened = seq[R:2 * R]
-    res = []
+    # open loop: Poisson arrivals at each load x saturated throughput, R requests each
+    runs = []
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        t0 = time.perf_counter()
-        i = 0
-        while i < len(opened):
-            now = time.perf_counter() - t0
-            while i < len(opened) and arrivals[i] <= now:
-                gi, up = opened[i]
-                srv.submit(gids[gi], up)
-                i += 1
-            r = srv.poll()
-            if r.size:
-                res.append(r)
-        res.append(srv.drain())
-        t_open = time.perf_counter() - t0
-    res = np.concatenate(res)
-    lat = res["latency_ns"] / 1e6
+        for li, load in enumerate(loads):
+            lam = load * sat
+            gaps = -np.log(1.0 - synth.Rng(seed + 1 + li).unit(R)) / lam
+            arrivals = np.cumsum(gaps)
+            opened = seq[(1 + li) * R:(2 + li) * R]
+            res = []
+            t0 = time.perf_counter()
+            i = 0
+            while i < len(opened):
+                now = time.perf_counter() - t0
+                while i < len(opened) and arrivals[i] <= now:
+                    gi, up = opened[i]
+                    srv.submit(gids[gi], up)
+                    i += 1
+                r = srv.poll()
+                if r.size:
+                    res.append(r)
+            res.append(srv.drain())
+            t_open = time.perf_counter() - t0
+            res = np.concatenate(res)
+            lat = res["latency_ns"] / 1e6
+            runs.append({"load": load, "lambda_per_s": lam, "updates_per_s": len(opened) / t_open,
+                         "seconds": t_open, "requests": len(opened),
+                         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                        "max": float(lat.max())},
+                         "failures": int((res["status"] != 0).sum())})
+    head = min(runs, key=lambda r: abs(r["load"] - 0.8))
     st = srv.stats()
     line = {"metric": "serving: updates/sec and p50/p99 latency over resident graphs",
-            "value": len(opened) / t_open, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
-            "ms_per_step": t_open * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": head["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": head["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32/u64/f64", "data": "synthetic",
             "config": {"workload": f"{G} graphs n log-uniform [1024,8192], ER/BA, w~U[1,100], "
-                                   f"{R} closed-loop then {R} Poisson requests (half edge, half vertex k 2..16)",
-                       "state_gb": state / 1e9, "saturated_updates_per_s": sat, "load": args.serve_load,
-                       "lambda_per_s": lam},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "closed_loop_failures": int((res_c["status"] != 0).sum()), "open_loop_failures": int((res["status"] != 0).sum()),
+                                   f"{R} closed-loop then {R} Poisson requests per load (half edge, half vertex k 2..16)",
+                       "state_gb": state / 1e9, "saturated_updates_per_s": sat, "load": head["load"],
+                       "lambda_per_s": head["lambda_per_s"]},
+            "latency_ms": head["latency_ms"], "loads": runs,
+            "closed_loop_failures": int((res_c["status"] != 0).sum()),
+            "open_loop_failures": sum(r["failures"] for r in runs),
             "server": st, "clocks": clk.summary()}
     print(json.dumps(line))
     return 0
@@ -689,6 +780,8 @@ def main():
     ap.add_argument("--serve-graphs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95",
+                    help="comma-separated loads (x saturated throughput) of the open-loop runs")
     ap.add_argument("--batch-graphs", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="sources of the all-core CPU oracle sample (cpu_baseline)")
@@ -697,6 +790,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1024,
                     help="sources recomputed per step of the reference arm")
     ap.add_argument("--recompute-runs", type=int, default=3)
+    ap.add_argument("--effective-updates", type=int, default=64,
+                    help="complete-graph workload: effective decreases in the variant run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--ncu-case", choices=["accumulate", "pair", "walk", "scan"], default=None,
