@@ -37,6 +37,7 @@ struct bc_graph {
     int poison_status = BC_OK;
     std::string last_error;
     bool full_scan = false;
+    bool fused_edges = true;   // undirected edge updates in one pass over both directions
     // weights of every arc of G (G_D for undirected graphs)
     std::unordered_map<uint64_t, int64_t> wmap;
     // host mirror of the E* superset CSR
@@ -480,6 +481,14 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
     const int32_t k = (int32_t)ent.size();
     const int full = g->full_scan ? 1 : 0;
     const bool pair = d.pair_on != 0;
+    // an undirected edge update: one pass over both directions (the vector path of the
+    // rank-1 pass; every row's candidates taken from the state before the update)
+    const bool fused = !g->directed && k == 1 && !g->full_scan && g->fused_edges && g->n % (16 / g->dbytes) == 0;
+    if (fused) {
+        kin = kout = 0;
+        timed(g, 3, 1, [&] { launch_edge_prep(d, ent[0].x, v, ent[0].w); });
+        timed(g, 0, 1, [&] { launch_edge_scan(d); });
+    }
     if (kin) {
         timed(g, 3, 1, [&] { launch_alg4_in(d, v, d_ent, k); });
         timed(g, 4, 1, [&] { launch_compact(d, d.mark, 0, d.rows, d.counts, full, 0); });
@@ -645,21 +654,21 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     d.nrb_max = (n + kRowsPerBlock - 1) / kRowsPerBlock;
     d.g_arcs = arcs;
     if (g->dbytes == 4) {
-        int32_t *pD, *pfD, *pcD, *pgw;
+        int32_t *pD, *pfD, *pcD, *pcD2, *pgw;
         if ((rc = dalloc(g, &pD, nn)) || (rc = dalloc(g, &pfD, n)) || (rc = dalloc(g, &pcD, n)) ||
-            (rc = dalloc(g, &pgw, arcs))) {
+            (rc = dalloc(g, &pcD2, n)) || (rc = dalloc(g, &pgw, arcs))) {
             destroy_all(g);
             return fail(nullptr, rc, "device allocation failed");
         }
-        d.D = pD; d.fD = pfD; d.cD = pcD; d.g_w = pgw;
+        d.D = pD; d.fD = pfD; d.cD = pcD; d.cD2 = pcD2; d.g_w = pgw;
     } else {
-        int64_t *pD, *pfD, *pcD, *pgw;
+        int64_t *pD, *pfD, *pcD, *pcD2, *pgw;
         if ((rc = dalloc(g, &pD, nn)) || (rc = dalloc(g, &pfD, n)) || (rc = dalloc(g, &pcD, n)) ||
-            (rc = dalloc(g, &pgw, arcs))) {
+            (rc = dalloc(g, &pcD2, n)) || (rc = dalloc(g, &pgw, arcs))) {
             destroy_all(g);
             return fail(nullptr, rc, "device allocation failed");
         }
-        d.D = pD; d.fD = pfD; d.cD = pcD; d.g_w = pgw;
+        d.D = pD; d.fD = pfD; d.cD = pcD; d.cD2 = pcD2; d.g_w = pgw;
     }
     if ((rc = dalloc(g, &d.S, nn)) || (rc = dalloc(g, &d.Dl, nn)) || (rc = dalloc(g, &d.bc_hi, n)) ||
         (rc = dalloc(g, &d.bc_lo, n)) || (rc = dalloc(g, &d.g_off, n + 1)) || (rc = dalloc(g, &d.g_src, arcs)) ||
@@ -667,7 +676,7 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         (rc = dalloc(g, &d.err, 1)) || (rc = dalloc(g, &d.stats, kStats)) || (rc = dalloc(g, &d.mark, n)) ||
         (rc = dalloc(g, &d.changed, n)) || (rc = dalloc(g, &d.rows, n)) || (rc = dalloc(g, &d.acc_rows, n)) ||
         (rc = dalloc(g, &d.counts, 8)) || (rc = dalloc(g, &d.fS, n)) || (rc = dalloc(g, &d.fM, n)) ||
-        (rc = dalloc(g, &d.cS, n)) || (rc = dalloc(g, &d.cM, n)) ||
+        (rc = dalloc(g, &d.cS, n)) || (rc = dalloc(g, &d.cM, n)) || (rc = dalloc(g, &d.cS2, n)) ||
         (rc = dalloc(g, &d.partial, (size_t)d.nrb_max * n))) {
         destroy_all(g);
         return fail(nullptr, rc, "device allocation failed");
@@ -1004,6 +1013,10 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
     if (!g || !name) return BC_ERR_ARG;
     if (std::strcmp(name, "full_scan") == 0) {
         g->full_scan = value != 0;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "fused_edges") == 0) {
+        g->fused_edges = value != 0;
         return BC_OK;
     }
     if (std::strcmp(name, "profile") == 0) {

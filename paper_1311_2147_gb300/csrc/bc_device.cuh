@@ -258,6 +258,13 @@ struct ScanArgs {
     int32_t* err;
     int64_t* stats;        // [4] pairs with a lower distance [5] pairs with new tied paths [6] rows
     PairRec rec;           // when rec.tcnt is set: record the changed pairs (pair corrections)
+    // Second row list with its own column vector (the fused pass of an undirected edge
+    // update: the rows whose new paths use the edge as v -> u); rows2 = NULL: one list.
+    const int32_t* rows2;
+    const int32_t* count2;
+    const DT* cD2;
+    const uint64_t* cS2;
+    const uint64_t* cM2;
 };
 
 // The rank-1 rule of Lemma 2 / Lemma 4 for one pair, given the candidate distance
@@ -383,7 +390,8 @@ __device__ __forceinline__ void load_u64s(const uint64_t* p, uint64_t* o) {
 // of VN and so is n), and the changed counts written back together, so a vector costs
 // one round trip to memory instead of one per pair.
 template <typename DT>
-__device__ __forceinline__ unsigned rule_vec_masked(const ScanArgs<DT>& a, size_t rowoff, int t,
+__device__ __forceinline__ unsigned rule_vec_masked(const ScanArgs<DT>& a, const uint64_t* colS,
+                                                    const uint64_t* colM, size_t rowoff, int t,
                                                     typename Vec<DT>::T& dv, const typename Vec<DT>::T& cv,
                                                     int64_t rd, uint64_t rs, uint64_t rm, int& n_changed,
                                                     int& n_ties, int64_t* dold, uint64_t* sold) {
@@ -395,8 +403,8 @@ __device__ __forceinline__ unsigned rule_vec_masked(const ScanArgs<DT>& a, size_
     V::unpack(dv, dd);
     V::unpack(cv, cd);
     load_u64s<VN>(a.S + rowoff + t, sg);
-    load_u64s<VN>(a.cS + t, cs);
-    load_u64s<VN>(a.cM + t, cm);
+    load_u64s<VN>(colS + t, cs);
+    load_u64s<VN>(colM + t, cm);
     unsigned mask = 0;
 #pragma unroll
     for (int q = 0; q < VN; ++q) {

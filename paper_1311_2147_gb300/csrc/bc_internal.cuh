@@ -176,6 +176,8 @@ struct Dev {
     void* cD;            // [n] per-column distances from v (DT)
     uint64_t* cS;        // [n] per-column path counts from v
     uint64_t* cM;        // [n] per-column multiplier of a tie
+    void* cD2;           // [n] second column vector (fused undirected edge pass): distances (DT)
+    uint64_t* cS2;       // [n] its path counts
     ff* partial;         // [nrb * n] column partial sums
     int32_t nrb_max;     // row blocks of the BC reduction
     int32_t acc_grid;    // CTAs of the accumulation kernel
@@ -262,6 +264,8 @@ void launch_compact(const Dev& d, const uint8_t* mark, int clear, int32_t* rows,
 void launch_scan_in(const Dev& d, int32_t v);
 void launch_scan_out(const Dev& d, int32_t v);
 void launch_write_row(const Dev& d, int32_t v);
+void launch_edge_prep(const Dev& d, int32_t u, int32_t v, int64_t w);
+void launch_edge_scan(const Dev& d);
 void launch_estar_keep(const Dev& d, uint8_t* keep);
 PairRec pair_rec(const Dev& d);
 void launch_pair_lists(const Dev& d);

@@ -177,6 +177,10 @@ __device__ __forceinline__ ScanArgs<DT> batch_scan_args(const Dev& d, const Batc
     a.tie_rows = 0;
     a.tie_cols = 0;
     a.rec = PairRec{};   // the batched path re-accumulates every changed row
+    a.rows2 = nullptr;
+    a.count2 = nullptr;
+    a.cD2 = nullptr;
+    a.cS2 = a.cM2 = nullptr;
     if (phase == 0) {
         a.cD = (const DT*)d.D + (size_t)u.v * d.n;
         a.cS = d.S + (size_t)u.v * d.n;

@@ -152,7 +152,8 @@ __device__ __forceinline__ void cs_wait() { asm volatile("cp.async.wait_group %0
 __device__ __forceinline__ void cs_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // WHOLE: n is a multiple of the chunk width, so no column of a chunk lies past n.
-template <typename DT, bool WHOLE>
+// DUAL: two row lists, each with its own column vector (a.rows2 set).
+template <typename DT, bool WHOLE, bool DUAL>
 __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<DT> a, int nch) {
     using V = Vec<DT>;
     using VT = typename V::T;
@@ -166,13 +167,32 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
     const int tid = threadIdx.x;
     const int n = a.n;
     const int64_t INF = Inf<DT>::v;
-    const int cnt = *a.count;
-    const int gpc = (int)gridDim.x / nch;   // CTAs per column chunk
+    int gpc = (int)gridDim.x / nch;   // CTAs per column chunk
     const int c = (int)blockIdx.x % nch;
-    const int r0 = (int)blockIdx.x / nch;
-    if (blockIdx.x == 0 && tid == 0)
+    int r0 = (int)blockIdx.x / nch;
+    int cnt = *a.count;
+    bool second = false;   // this CTA works on the second list
+    if (DUAL) {
+        // two lists: the CTAs of a chunk are split between them in proportion to their
+        // lengths (at least one each when both have rows); this CTA takes the second
+        // list's column vector and rows when it falls in the second share
+        const int cnt2 = *a.count2;
+        int g1 = (cnt + cnt2) ? (int)(((int64_t)gpc * cnt + (cnt + cnt2) / 2) / (cnt + cnt2)) : gpc;
+        if (cnt > 0 && cnt2 > 0) g1 = min(max(g1, 1), gpc - 1);
+        if (blockIdx.x == 0 && tid == 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6), (unsigned long long)(cnt + cnt2));
+        if (r0 >= g1) {
+            r0 -= g1;
+            gpc -= g1;
+            cnt = cnt2;
+            second = true;
+        } else {
+            gpc = g1;
+        }
+    } else if (blockIdx.x == 0 && tid == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6), (unsigned long long)cnt);
-    if (r0 >= gpc || r0 >= cnt) return;   // block-uniform: no rows for this CTA
+    }
+    if (gpc <= 0 || r0 >= gpc || r0 >= cnt) return;   // block-uniform: no rows for this CTA
     const int t0 = c * CW;
     // the column chunk: quick-test values in registers; cmax = largest finite TRUE value
     // (the bound that makes the one-compare quick test overflow-free)
@@ -182,13 +202,13 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
     for (int u = 0; u < kCsVpt; ++u) {
         const int t = t0 + (u * kCsThreads + tid) * VN;
         if (WHOLE || t < n) {
-            VT x = __ldg(reinterpret_cast<const VT*>(a.cD + t));
+            VT x = __ldg(reinterpret_cast<const VT*>(((DUAL && second) ? a.cD2 : a.cD) + t));
             int64_t xv[VN];
             V::unpack(x, xv);
 #pragma unroll
             for (int q = 0; q < VN; ++q) {
                 if (xv[q] != INF && xv[q] > m) m = xv[q];
-                if (a.tie_cols && xv[q] < INF - 1 && __ldg(a.cM + t + q) == 0ull) V::set(x, q, xv[q] + 1);
+                if (a.tie_cols && xv[q] < INF - 1 && __ldg(((DUAL && second) ? a.cM2 : a.cM) + t + q) == 0ull) V::set(x, q, xv[q] + 1);
             }
             cq[u] = x;
         }
@@ -206,7 +226,7 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
     // the issue never waits for them), and the issue takes its row's values by shuffle.
     // Per stage: the row it holds and that row's scalars (consumed ST rows later).
     const int lane = tid & 31;
-    auto batch_row = [&](int k) { return k < nk ? a.rows[r0 + k * gpc] : -1; };
+    auto batch_row = [&](int k) { return k < nk ? ((DUAL && second) ? a.rows2 : a.rows)[r0 + k * gpc] : -1; };
     int cur_s = batch_row(lane), nxt_s = batch_row(32 + lane);
     DT cur_d = cur_s >= 0 ? a.fD[cur_s] : (DT)0;
     DT nxt_d = nxt_s >= 0 ? a.fD[nxt_s] : (DT)0;
@@ -259,8 +279,9 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
             const int64_t rd = (int64_t)a.fD[s];
             const uint64_t rs = a.fS[s], rm = a.fM[s];
             VT dv = *reinterpret_cast<const VT*>(a.D + rowoff + t);
-            const VT cv = __ldg(reinterpret_cast<const VT*>(a.cD + t));
-            const unsigned m = rule_vec_masked<DT>(a, rowoff, t, dv, cv, rd, rs, rm, n_changed, n_ties, dold, sold);
+            const VT cv = __ldg(reinterpret_cast<const VT*>(((DUAL && second) ? a.cD2 : a.cD) + t));
+            const unsigned m = rule_vec_masked<DT>(a, second ? a.cS2 : a.cS, second ? a.cM2 : a.cM, rowoff, t, dv, cv,
+                                                   rd, rs, rm, n_changed, n_ties, dold, sold);
             if (m & 0xffu) *reinterpret_cast<VT*>(a.D + rowoff + t) = dv;
             bits = (m | (m >> 8)) & 0xffu;
         }
@@ -368,6 +389,79 @@ __global__ void k_estar_keep(int n, const DT* D, const int32_t* e_src, const Arc
     keep[e] = (a.dst >= 0 && (int64_t)D[(size_t)e_src[e] * n + a.dst] == (int64_t)a.w) ? 1 : 0;
 }
 
+// Fused pass of an undirected edge update {u, v} with weight w, preparation (one thread
+// per row s): snapshot rows u and v of the state before the update (the column vectors
+// of the pass; in G_D row x holds d(x, .) = d(., x), so position s of rows u and v also
+// gives d(s,u) and d(s,v)), and put row s on one of two lists by the direction in which
+// a new shortest path would use the edge:
+//   list 1 (s ~> u -> v):  d(s,u) + w <= d(s,v);   list 2 (s ~> v -> u):  d(s,v) + w <= d(s,u).
+// No row is on both (that would need 2w <= 0).  Per row it writes what Algorithm 4 with
+// the one in-edge gives for the row's direction: the distance through the edge, the
+// path count to the far endpoint and the tie multiplier (Lemma 2: on a tie only the new
+// paths are added).  A shortest simple path uses the edge in at most one direction, and
+// a candidate whose prefix already used the edge the other way is longer than d(s,t),
+// so one pass with both candidates taken from the old state gives the two directed
+// passes' d and sigma.  Rows are appended with one atomic per warp and list (the counts
+// start at zero); the order of a list does not affect any result.
+template <typename DT>
+__global__ void k_edge_prep(int n, const DT* D, const uint64_t* S, int u, int v, int64_t w, DT* cDv,
+                            uint64_t* cSv, DT* cDu, uint64_t* cSu, DT* fD, uint64_t* fS, uint64_t* fM,
+                            int32_t* rows1, int32_t* count1, int32_t* rows2, int32_t* count2,
+                            uint8_t* changed, int32_t* err) {
+    if (*reinterpret_cast<const volatile int32_t*>(err)) return;   // grid-uniform for this launch
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t INF = Inf<DT>::v;
+    bool in1 = false, in2 = false;
+    if (s < n) {
+        const int64_t du = D[(size_t)u * n + s], dv = D[(size_t)v * n + s];
+        const uint64_t su = S[(size_t)u * n + s], sv = S[(size_t)v * n + s];
+        cDu[s] = (DT)du;
+        cSu[s] = su;
+        cDv[s] = (DT)dv;
+        cSv[s] = sv;
+        int64_t rd = 0;
+        uint64_t rs = 0, rm = 0;
+        if (du != INF) {
+            const int64_t c = dsum<DT>(du, w);
+            if (c == SAT) {
+                if (dv == INF) set_err(err, ERRF_DIST);
+            } else if (c < dv) {
+                in1 = true; rd = c; rs = su; rm = su;
+            } else if (c == dv) {
+                in1 = true; rd = c; rs = add_chk(sv, su, err); rm = su;
+            }
+        }
+        if (!in1 && dv != INF) {
+            const int64_t c = dsum<DT>(dv, w);
+            if (c == SAT) {
+                if (du == INF) set_err(err, ERRF_DIST);
+            } else if (c < du) {
+                in2 = true; rd = c; rs = sv; rm = sv;
+            } else if (c == du) {
+                in2 = true; rd = c; rs = add_chk(su, sv, err); rm = sv;
+            }
+        }
+        if (in1 || in2) {
+            fD[s] = (DT)rd;
+            fS[s] = rs;
+            fM[s] = rm;
+            changed[s] = 1;
+        }
+    }
+    const unsigned b1 = __ballot_sync(0xffffffffu, in1), b2 = __ballot_sync(0xffffffffu, in2);
+    int p1 = 0, p2 = 0;
+    if (lane == 0) {
+        if (b1) p1 = atomicAdd(count1, __popc(b1));
+        if (b2) p2 = atomicAdd(count2, __popc(b2));
+    }
+    p1 = __shfl_sync(0xffffffffu, p1, 0);
+    p2 = __shfl_sync(0xffffffffu, p2, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (in1) rows1[p1 + __popc(b1 & lt)] = s;
+    if (in2) rows2[p2 + __popc(b2 & lt)] = s;
+}
+
 // ------------------------------------------------------------------ launches
 
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -431,14 +525,15 @@ constexpr size_t kCsSmem = kCsRingBytes + (size_t)(kCsThreads / 32) * 64 * sizeo
 // Allows the vector-path kernels their shared memory on the current device.
 cudaError_t scan_setup() {
     const int b = (int)kCsSmem;
-    cudaError_t e = cudaFuncSetAttribute(k_scan_cs<int32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_scan_cs<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_scan_cs<int64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_scan_cs<int64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    return e;
+    const void* fns[] = {(const void*)k_scan_cs<int32_t, true, false>, (const void*)k_scan_cs<int32_t, false, false>,
+                         (const void*)k_scan_cs<int64_t, true, false>, (const void*)k_scan_cs<int64_t, false, false>,
+                         (const void*)k_scan_cs<int32_t, true, true>,  (const void*)k_scan_cs<int32_t, false, true>,
+                         (const void*)k_scan_cs<int64_t, true, true>,  (const void*)k_scan_cs<int64_t, false, true>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename DT>
@@ -448,10 +543,14 @@ static void scan_dispatch(const Dev& d, ScanArgs<DT> a) {
         constexpr int CW = kCsThreads * kCsVpt * VN;
         const int nch = (d.n + CW - 1) / CW;
         const int per = std::max(1, d.nsm * kCsCtasPerSm / nch);
-        if (d.n % CW == 0)
-            k_scan_cs<DT, true><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
-        else
-            k_scan_cs<DT, false><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+        const bool whole = d.n % CW == 0;
+        if (a.rows2) {
+            if (whole) k_scan_cs<DT, true, true><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+            else k_scan_cs<DT, false, true><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+        } else {
+            if (whole) k_scan_cs<DT, true, false><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+            else k_scan_cs<DT, false, false><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+        }
     } else {
         k_scan<DT, false><<<d.nsm * 8, kScanThreads, 0, d.st>>>(a);
     }
@@ -471,6 +570,10 @@ static ScanArgs<DT> scan_args(const Dev& d) {
     a.skip_row = -1;
     a.tie_rows = 0;
     a.tie_cols = 0;
+    a.rows2 = nullptr;
+    a.count2 = nullptr;
+    a.cD2 = nullptr;
+    a.cS2 = a.cM2 = nullptr;
     a.err = d.err;
     a.stats = d.stats;
     a.rec = d.pair_on ? pair_rec(d) : PairRec{};
@@ -532,6 +635,45 @@ void launch_write_row(const Dev& d, int32_t v) {
     else
         k_write_row<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int64_t*)d.D, d.S, v,
                                                                 (const int64_t*)d.cD, d.cS, rec, d.err);
+}
+
+// The fused pass of an undirected edge update {u, v} with weight w: the row lists and
+// column snapshots (k_edge_prep), then one rank-1 pass over both lists, each against its
+// own column vector, every change a first change of the update.  List 1 goes to rows /
+// counts[0] against row v; list 2 to acc_rows / counts[2] (free until the pair lists are
+// built after the pass) against row u.
+void launch_edge_prep(const Dev& d, int32_t u, int32_t v, int64_t w) {
+    cudaMemsetAsync(d.counts, 0, 3 * sizeof(int32_t), d.st);   // counts[0..2]; [1] is rewritten later
+    const int grid = (d.n + 255) / 256;
+    if (d.dbytes == 4)
+        k_edge_prep<int32_t><<<grid, 256, 0, d.st>>>(
+            d.n, (const int32_t*)d.D, d.S, u, v, w, (int32_t*)d.cD, d.cS, (int32_t*)d.cD2, d.cS2, (int32_t*)d.fD,
+            d.fS, d.fM, d.rows, d.counts, d.acc_rows, d.counts + 2, d.changed, d.err);
+    else
+        k_edge_prep<int64_t><<<grid, 256, 0, d.st>>>(
+            d.n, (const int64_t*)d.D, d.S, u, v, w, (int64_t*)d.cD, d.cS, (int64_t*)d.cD2, d.cS2, (int64_t*)d.fD,
+            d.fS, d.fM, d.rows, d.counts, d.acc_rows, d.counts + 2, d.changed, d.err);
+}
+
+template <typename DT>
+static void edge_scan(const Dev& d) {
+    ScanArgs<DT> a = scan_args<DT>(d);
+    a.rec.first = 1;
+    a.tie_rows = 1;
+    a.cD = (const DT*)d.cD;
+    a.cS = d.cS;
+    a.cM = d.cS;
+    a.rows2 = d.acc_rows;
+    a.count2 = d.counts + 2;
+    a.cD2 = (const DT*)d.cD2;
+    a.cS2 = d.cS2;
+    a.cM2 = d.cS2;
+    scan_dispatch<DT>(d, a);
+}
+
+void launch_edge_scan(const Dev& d) {
+    if (d.dbytes == 4) edge_scan<int32_t>(d);
+    else edge_scan<int64_t>(d);
 }
 
 void launch_estar_keep(const Dev& d, uint8_t* keep) {
