@@ -66,7 +66,8 @@ enum {
     BC_DIRECTED = 1,
     BC_UNDIRECTED = 2,
     BC_DIST_I32 = 16,
-    BC_DIST_I64 = 32
+    BC_DIST_I64 = 32,
+    BC_STATIC_ALL_ARCS = 64      /* bc_init_static: search every arc (no E* pruning) */
 };
 
 enum { BC_UPD_EDGE = 0, BC_UPD_VERTEX = 1 };
@@ -136,8 +137,14 @@ typedef struct bc_info {
  *   m            number of edges in src/dst/w (undirected: each edge once).
  *   src,dst,w    host arrays of m entries; w in [1, INF-1] of the distance type.
  *   flags        exactly one of BC_DIRECTED / BC_UNDIRECTED, and one of
- *                BC_DIST_I32 / BC_DIST_I64.
+ *                BC_DIST_I32 / BC_DIST_I64; optionally BC_STATIC_ALL_ARCS.
  *   cuda_stream  a cudaStream_t (NULL = legacy default stream).
+ * The all-pairs distances come from one search per source (one CTA each).  By default
+ * the searches are restricted to E* as it becomes known (Section 6, Algorithm 6 step
+ * 1, whose Hidden Paths algorithm examines only arcs of E*): once the search from a
+ * has finished, the arcs (a,b) with w(a,b) > d(a,b) are left out of every later search,
+ * and the sources run highest out-degree first.  BC_STATIC_ALL_ARCS searches every
+ * arc instead (the same results; kept for comparison).
  * Synchronous.  Returns BC_ERR_ARG for a malformed graph or flags, BC_ERR_OOM when
  * the n x n state does not fit, and the device-side errors above.
  */

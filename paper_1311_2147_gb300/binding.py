@@ -27,6 +27,7 @@ BC_DIRECTED = 1
 BC_UNDIRECTED = 2
 BC_DIST_I32 = 16
 BC_DIST_I64 = 32
+BC_STATIC_ALL_ARCS = 64
 BC_UPD_EDGE = 0
 BC_UPD_VERTEX = 1
 
@@ -158,7 +159,7 @@ def encode_updates(ups):
 class BCGraph:
     """One device-resident graph state."""
 
-    def __init__(self, g, dist: str = "i32", stream=None):
+    def __init__(self, g, dist: str = "i32", stream=None, static_all_arcs: bool = False):
         lib = load()
         self.lib = lib
         self.n = int(g.n)
@@ -167,6 +168,8 @@ class BCGraph:
         dst = np.ascontiguousarray(g.dst, dtype=np.int32)
         w = np.ascontiguousarray(g.w, dtype=np.int64)
         flags = (BC_DIRECTED if self.directed else BC_UNDIRECTED) | (BC_DIST_I32 if dist == "i32" else BC_DIST_I64)
+        if static_all_arcs:
+            flags |= BC_STATIC_ALL_ARCS
         h = ctypes.c_void_p()
         st = None if stream is None else ctypes.c_void_p(int(stream))
         rc = lib.bc_init_static(ctypes.byref(h), self.n, int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(w),

@@ -753,7 +753,21 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     } else {
         CKI(cudaMemcpyAsync(d.g_w, cw.data(), sizeof(int64_t) * arcs, cudaMemcpyHostToDevice, d.st));
     }
-    // all-pairs distances, then E* read off them
+    // all-pairs distances, then E* read off them.  Unless asked for the search over every
+    // arc, arcs found outside E* are pruned as the searches finish (k_static.cu), the
+    // sources running highest out-degree first.
+    const bool prune = (flags & BC_STATIC_ALL_ARCS) == 0 && arcs > 0;
+    if (prune) {
+        std::vector<int32_t> order(n);
+        for (int32_t i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return off[a + 1] - off[a] > off[b + 1] - off[b];
+        });
+        if ((rc = dalloc(g, &d.p_dst, arcs)) || (rc = dalloc(g, &d.s_order, n)))
+            return bail(rc, "device allocation failed");
+        CKI(cudaMemcpyAsync(d.p_dst, d.g_dst, sizeof(int32_t) * arcs, cudaMemcpyDeviceToDevice, d.st));
+        CKI(cudaMemcpyAsync(d.s_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, d.st));
+    }
     launch_sssp(d);
     uint8_t* d_flags = nullptr;
     if ((rc = dalloc(g, &d_flags, arcs))) return bail(rc, "device allocation failed");
@@ -764,6 +778,12 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
     CKI(cudaGetLastError());
     dfree(g, d_flags);
     g->bytes -= (int64_t)std::max<int64_t>(arcs, 1);
+    if (prune) {
+        dfree(g, d.p_dst);
+        dfree(g, d.s_order);
+        g->bytes -= 4 * (int64_t)std::max<int64_t>(arcs, 1) + 4 * (int64_t)n;
+        d.p_dst = d.s_order = nullptr;
+    }
     {
         std::vector<HArc> estar;
         for (int64_t i = 0; i < arcs; ++i)

@@ -152,6 +152,8 @@ struct Dev {
     int32_t* g_src;
     int32_t* g_dst;
     void* g_w;
+    int32_t* p_dst;      // static search: working copy of g_dst pruned to E* (NULL: no pruning)
+    int32_t* s_order;    // static search: sources in order (NULL: 0 .. n-1)
     int64_t g_arcs;
     // E*+ CSR with slack
     int32_t* e_off;

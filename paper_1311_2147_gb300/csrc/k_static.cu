@@ -12,6 +12,19 @@
 // E* (Section 1: arcs on some shortest path) is then {(a,b) : w(a,b) = d(a,b)}: the
 // one-arc path a->b is shortest exactly when the arc lies on a shortest path (a
 // sub-path of a shortest path is shortest).
+//
+// E* pruning (Section 6, Algorithm 6 step 1: the Hidden Paths algorithm examines only
+// arcs of E*).  A search from s needs only the arcs of E* (every shortest path is made
+// of them), and an arc (a,b) is known to be in E* or not as soon as the search from a
+// has finished: w(a,b) = d(a,b).  So with pruning on, the CTA that finishes the
+// search from a overwrites the head of every arc of a that is not in E* with -1 in a
+// working copy of the arc heads, and every later search skips those arcs.  A search
+// that reads a head while it is being overwritten sees either the head or -1; both are
+// correct, since a search may use any set of arcs that contains E*.  The sources run in
+// the given order, highest out-degree first, so that most arcs are decided early.
+// (Hidden Paths settles the pairs of all sources in one global distance order and so
+// never examines an arc outside E*; this form examines each arc at most until its
+// tail's own search has finished.)
 #include "bc_internal.cuh"
 
 namespace bcg {
@@ -28,10 +41,12 @@ __device__ __forceinline__ int64_t atomic_min_dt(int64_t* p, int64_t v) {
     return (int64_t)atomicMin(reinterpret_cast<long long*>(p), (long long)v);
 }
 
+// order: the sources in the order to run them (NULL: 0 .. n-1).  pdst: the working
+// copy of the arc heads to prune (NULL: every arc is searched, dst is read).
 template <typename DT, bool SMEM_DIST>
 __global__ void __launch_bounds__(kSsspThreads)
 k_sssp(int n, const int32_t* __restrict__ off, const int32_t* __restrict__ dst,
-       const DT* __restrict__ w, DT* D, int32_t* err) {
+       const DT* __restrict__ w, DT* D, int32_t* err, const int32_t* __restrict__ order, int32_t* pdst) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int words = (n + 31) >> 5;
     DT* dist_s = reinterpret_cast<DT*>(smem);
@@ -41,8 +56,10 @@ k_sssp(int n, const int32_t* __restrict__ off, const int32_t* __restrict__ dst,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = kSsspThreads / 32;
     const int64_t INF = Inf<DT>::v;
-    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    const int32_t* heads = pdst ? pdst : dst;
+    for (int si = blockIdx.x; si < n; si += gridDim.x) {
         if (block_err(err)) return;
+        const int s = order ? order[si] : si;
         DT* dist = SMEM_DIST ? dist_s : D + (size_t)s * n;
         for (int t = tid; t < n; t += kSsspThreads) dist[t] = (t == s) ? (DT)0 : (DT)INF;
         for (int q = tid; q < words; q += kSsspThreads) {
@@ -61,7 +78,8 @@ k_sssp(int n, const int32_t* __restrict__ off, const int32_t* __restrict__ dst,
                     const int64_t dx = ld_relaxed(dist + x);
                     const int end = off[x + 1];
                     for (int e = off[x] + lane; e < end; e += 32) {
-                        const int b = dst[e];
+                        const int b = ld_relaxed(heads + e);
+                        if (b < 0) continue;   // pruned: not in E*
                         const int64_t nd = dsum<DT>(dx, (int64_t)w[e]);
                         if (nd == SAT) {
                             s_sat = 1;
@@ -104,6 +122,12 @@ k_sssp(int n, const int32_t* __restrict__ off, const int32_t* __restrict__ dst,
             DT* row = D + (size_t)s * n;
             for (int t = tid; t < n; t += kSsspThreads) row[t] = dist_s[t];
         }
+        // the search from s is final: the arcs of s with w(s,b) > d(s,b) are not in E*
+        if (pdst)
+            for (int e = off[s] + tid; e < off[s + 1]; e += kSsspThreads) {
+                const int b = dst[e];
+                if ((int64_t)w[e] != ld_relaxed(dist + b)) pdst[e] = -1;
+            }
         __syncthreads();
     }
 }
@@ -130,7 +154,7 @@ static void sssp_dispatch(const Dev& d) {
         if (per_sm < 1) per_sm = 1;
         const int grid = (int)std::min<int64_t>((int64_t)d.nsm * per_sm, d.n);
         k_sssp<DT, true><<<grid, kSsspThreads, smem, d.st>>>(d.n, d.g_off, d.g_dst, (const DT*)d.g_w,
-                                                             (DT*)d.D, d.err);
+                                                             (DT*)d.D, d.err, d.s_order, d.p_dst);
     } else {
         const size_t smem = bitmaps;
         cudaFuncSetAttribute(k_sssp<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -139,7 +163,7 @@ static void sssp_dispatch(const Dev& d) {
         if (per_sm < 1) per_sm = 1;
         const int grid = (int)std::min<int64_t>((int64_t)d.nsm * per_sm, d.n);
         k_sssp<DT, false><<<grid, kSsspThreads, smem, d.st>>>(d.n, d.g_off, d.g_dst, (const DT*)d.g_w,
-                                                              (DT*)d.D, d.err);
+                                                              (DT*)d.D, d.err, d.s_order, d.p_dst);
     }
 }
 
