@@ -267,6 +267,36 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
 int bc_set_option(bc_graph* g, const char* name, int64_t value);
 
 /*
+ * Real (fp64) weights.  Section 2 allows positive real weights; Lemma 2 and Lemma 4
+ * compare path lengths for equality, so ties must be decided exactly.  A finite
+ * double w > 0 is exactly M * 2^e (M an odd integer below 2^53); with E the smallest e
+ * over the graph's weights every weight is an integer number of units of 2^E, and so
+ * is every path length.  These calls run the state on those integers, so path lengths
+ * are the exact sums of the given doubles and two paths tie exactly when those sums
+ * are equal (0.1 + 0.2 does not tie with 0.3: as doubles they differ).  BC does not
+ * depend on the unit.
+ *
+ * bc_init_static_f64 -- as bc_init_static with w a host array of m doubles, each
+ *   finite and > 0.  BC_ERR_ARG when a weight is not, or when the weights span too
+ *   many binary orders of magnitude: n - 1 copies of the largest weight, in units of
+ *   the smallest power of two, must fit the distance type (30 bits for BC_DIST_I32,
+ *   62 for BC_DIST_I64).
+ * bc_apply_edge_update_f64 / bc_apply_vertex_update_f64 -- as bc_apply_edge_update /
+ *   bc_apply_vertex_update with double weights, on a handle made by
+ *   bc_init_static_f64.  BC_ERR_ARG (state untouched) for a weight that is not a whole
+ *   number of the handle's units or exceeds the size bound above.
+ * bc_get_weight_unit -- *exp2 = E: the distances of bc_get_rows, and the weights of
+ *   bc_get_edges and bc_apply_updates, are integers in units of 2^E (0 for a handle
+ *   made by bc_init_static).
+ */
+int bc_init_static_f64(bc_graph** out, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                       const double* w, uint32_t flags, void* cuda_stream);
+int bc_apply_edge_update_f64(bc_graph* g, int32_t u, int32_t v, double w_new);
+int bc_apply_vertex_update_f64(bc_graph* g, int32_t v, int32_t k, const int32_t* nbr, const double* w_new,
+                               const uint8_t* dir);
+int bc_get_weight_unit(bc_graph* g, int32_t* exp2);
+
+/*
  * bc_static_scores_noalloc -- BC(v) of a small graph that is already in device memory,
  * computed without allocating any device memory.  (The paper has no counterpart: this
  * serves callers that cannot call cudaMalloc -- a process whose device memory belongs to

@@ -44,7 +44,8 @@ EXPORTS = ["bc_init_static", "bc_apply_edge_update", "bc_apply_vertex_update", "
            "bc_static_scores_noalloc", "bc_batch_create", "bc_batch_apply", "bc_batch_set_tiles",
            "bc_batch_last_ms", "bc_batch_last_error", "bc_batch_destroy", "bc_get_edges",
            "bc_server_create", "bc_server_add_graph", "bc_server_submit", "bc_server_poll",
-           "bc_server_pending", "bc_server_graph", "bc_server_stats", "bc_server_destroy"]
+           "bc_server_pending", "bc_server_graph", "bc_server_stats", "bc_server_destroy",
+           "bc_init_static_f64", "bc_apply_edge_update_f64", "bc_apply_vertex_update_f64", "bc_get_weight_unit"]
 PROFILE_CLASSES = ["scan", "accumulate", "bc_rows", "vertex_passes", "bookkeeping", "pair_corrections"]
 
 
@@ -125,6 +126,10 @@ def load(build_if_missing: bool = True):
         "bc_server_graph": ([p, i32, ctypes.POINTER(p)], ctypes.c_int),
         "bc_server_stats": ([p, p], ctypes.c_int),
         "bc_server_destroy": ([p], None),
+        "bc_init_static_f64": ([ctypes.POINTER(p), i32, i64, p, p, p, u32, p], ctypes.c_int),
+        "bc_apply_edge_update_f64": ([p, i32, i32, ctypes.c_double], ctypes.c_int),
+        "bc_apply_vertex_update_f64": ([p, i32, i32, p, p, p], ctypes.c_int),
+        "bc_get_weight_unit": ([p, ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +266,42 @@ class BCGraph:
 
     def last_error(self):
         return self.lib.bc_last_error(self.h).decode()
+
+
+class BCGraphReal(BCGraph):
+    """A device-resident graph state with real (fp64) weights: path lengths are the
+    exact sums of the given doubles (bc_init_static_f64)."""
+
+    def __init__(self, n, directed, src, dst, w, dist: str = "i64", stream=None):
+        lib = load()
+        self.lib = lib
+        self.n = int(n)
+        self.directed = bool(directed)
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        flags = (BC_DIRECTED if self.directed else BC_UNDIRECTED) | (BC_DIST_I32 if dist == "i32" else BC_DIST_I64)
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = lib.bc_init_static_f64(ctypes.byref(h), self.n, int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(w),
+                                    flags, st)
+        if rc != BC_OK:
+            raise BCError(rc, lib.bc_last_error(None).decode())
+        self.h = h
+
+    def bc_apply_edge_update_f64(self, u, v, w):
+        return self.lib.bc_apply_edge_update_f64(self.h, int(u), int(v), float(w))
+
+    def bc_apply_vertex_update_f64(self, v, nbr, w, dirs=None):
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        d = None if dirs is None else np.ascontiguousarray(dirs, dtype=np.uint8)
+        return self.lib.bc_apply_vertex_update_f64(self.h, int(v), int(nbr.shape[0]), _ptr(nbr), _ptr(w), _ptr(d))
+
+    def bc_get_weight_unit(self):
+        e = ctypes.c_int32(0)
+        self._check(self.lib.bc_get_weight_unit(self.h, ctypes.byref(e)))
+        return e.value
 
 
 class BCBatch:

@@ -1,6 +1,7 @@
 // bc_api.cu -- host side of libbcgpu.so: handles, validation, the E* superset and the
 // launch sequence of every update.  Declarations and conventions: include/bcgpu.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -38,6 +39,11 @@ struct bc_graph {
     std::string last_error;
     bool full_scan = false;
     bool fused_edges = true;   // undirected edge updates in one pass over both directions
+    // real weights (bc_init_static_f64): every weight is an integer number of units of
+    // 2^w_exp; top_bits bounds their size (weights below 2^top_bits units)
+    bool real_weights = false;
+    int32_t w_exp = 0;
+    int32_t top_bits = 0;
     // weights of every arc of G (G_D for undirected graphs)
     std::unordered_map<uint64_t, int64_t> wmap;
     // host mirror of the E* superset CSR
@@ -934,6 +940,100 @@ int bc_apply_vertex_update(bc_graph* g, int32_t v, int32_t k, const int32_t* nbr
     for (int32_t j = 0; j < k; ++j) e[j] = {nbr[j], dir ? (int32_t)dir[j] : 0, w_new[j]};
     bc_update up{BC_UPD_VERTEX, -1, v, k, 0, 0};
     return bc_apply_updates(g, 1, &up, e.data(), k, nullptr);
+}
+
+// ---- real (fp64) weights
+//
+// A finite double w > 0 is exactly M * 2^e with M an odd integer below 2^53.  With E the
+// smallest such e over the weights, every weight is the integer (w / 2^E) units of 2^E,
+// exactly, and so is every path length: path lengths are compared, and ties decided, on
+// the exact sums of the given doubles.  The state runs on these integers; BC does not
+// depend on the unit.  The weights must span few enough binary orders of magnitude that
+// n - 1 of the largest one fit the distance type.
+static bool split_double(double w, int32_t* e_low, int32_t* e_top) {
+    if (!(w > 0.0) || !std::isfinite(w)) return false;
+    int x = 0;
+    const double f = std::frexp(w, &x);                 // w = f * 2^x, f in [0.5, 1)
+    uint64_t mant = (uint64_t)std::ldexp(f, 53);        // exact: w = mant * 2^(x - 53)
+    int tz = 0;
+    while (!(mant & 1ull)) { mant >>= 1; ++tz; }
+    *e_low = x - 53 + tz;                               // w = odd * 2^e_low
+    *e_top = x;                                         // w < 2^e_top
+    return true;
+}
+
+static int bits_for(int64_t n) {
+    int b = 0;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+// w as an integer number of units 2^e (exact), or -1 when it is not a multiple of the
+// unit or not below 2^top units.
+static int64_t to_units(double w, int32_t e, int32_t top) {
+    int32_t lo = 0, hi = 0;
+    if (!split_double(w, &lo, &hi) || lo < e || hi - e > top) return -1;
+    return (int64_t)std::ldexp(w, -e);
+}
+
+int bc_init_static_f64(bc_graph** out, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                       const double* w, uint32_t flags, void* cuda_stream) {
+    if (!out) return fail(nullptr, BC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || m < 0 || (m > 0 && (!src || !dst || !w))) return fail(nullptr, BC_ERR_ARG, "bad edge arrays");
+    const bool i32 = (flags & BC_DIST_I32) != 0;
+    int32_t e_min = INT32_MAX, top = INT32_MIN;
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t lo = 0, hi = 0;
+        if (!split_double(w[i], &lo, &hi)) return fail(nullptr, BC_ERR_ARG, "a weight is not a finite positive double");
+        e_min = std::min(e_min, lo);
+        top = std::max(top, hi);
+    }
+    if (m == 0) e_min = top = 0;
+    // the largest weight is below 2^(top - e_min) units; n - 1 of them must stay below
+    // INF of the distance type (2^31 - 1 or 2^63 - 1)
+    const int32_t span = top - e_min;
+    if (span + bits_for(n) > (i32 ? 30 : 62))
+        return fail(nullptr, BC_ERR_ARG, "weights span too many binary orders of magnitude for exact sums");
+    std::vector<int64_t> wi((size_t)m);
+    for (int64_t i = 0; i < m; ++i) wi[i] = (int64_t)std::ldexp(w[i], -e_min);
+    const int rc = bc_init_static(out, n, m, src, dst, wi.data(), flags, cuda_stream);
+    if (rc) return rc;
+    (*out)->real_weights = true;
+    (*out)->w_exp = e_min;
+    (*out)->top_bits = (i32 ? 30 : 62) - bits_for(n);
+    return BC_OK;
+}
+
+int bc_apply_edge_update_f64(bc_graph* g, int32_t u, int32_t v, double w_new) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (!g->real_weights) return fail(g, BC_ERR_ARG, "the handle was not made by bc_init_static_f64");
+    const int64_t x = to_units(w_new, g->w_exp, g->top_bits);
+    if (x < 1) return fail(g, BC_ERR_ARG, "weight not representable exactly in the handle's unit");
+    return bc_apply_edge_update(g, u, v, x);
+}
+
+int bc_apply_vertex_update_f64(bc_graph* g, int32_t v, int32_t k, const int32_t* nbr, const double* w_new,
+                               const uint8_t* dir) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (!g->real_weights) return fail(g, BC_ERR_ARG, "the handle was not made by bc_init_static_f64");
+    if (k < 1 || !w_new) return fail(g, BC_ERR_ARG, "bad vertex update arrays");
+    std::vector<int64_t> xi(k);
+    for (int32_t j = 0; j < k; ++j) {
+        xi[j] = to_units(w_new[j], g->w_exp, g->top_bits);
+        if (xi[j] < 1) return fail(g, BC_ERR_ARG, "weight not representable exactly in the handle's unit");
+    }
+    return bc_apply_vertex_update(g, v, k, nbr, xi.data(), dir);
+}
+
+int bc_get_weight_unit(bc_graph* g, int32_t* exp2) {
+    int rc;
+    if (!check_alive(g, &rc)) return rc;
+    if (!exp2) return fail(g, BC_ERR_ARG, "exp2 is NULL");
+    *exp2 = g->real_weights ? g->w_exp : 0;
+    return BC_OK;
 }
 
 int bc_get_scores(bc_graph* g, double* out) {
