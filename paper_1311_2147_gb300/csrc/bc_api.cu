@@ -521,14 +521,18 @@ int enqueue_update(bc_graph* g, int32_t v, const std::vector<VEdge>& ent, const 
         // made, which k_bc_fix folds into BC at the end
         if (!g->profile) {
             // the two write disjoint dependency rows and only read the rest of the state:
-            // the full rows' BC sums and (latency-bound, often partial-wave)
-            // accumulation run on the second stream beside the pair corrections, which
-            // do not touch BC itself until k_bc_fix, after the join
+            // the (latency-bound, partial-wave) accumulation of the full rows and their
+            // new BC sums run on the second stream beside the pair corrections, which do
+            // not touch BC itself until k_bc_fix, after the join.  The old rows' BC sums
+            // are taken first on this stream, so that the accumulation is the first
+            // kernel of the second stream: launched before the pair corrections, it gets
+            // its SMs before their CTAs (which stay resident until all their work is
+            // taken) fill the GPU.
             Dev ds = d;
             ds.st = g->side;
+            launch_bc_rows_list(d, -1, d.full_rows, d.counts + 3);
             CK(g, cudaEventRecord(g->ev_fork, d.st));
             CK(g, cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-            launch_bc_rows_list(ds, -1, d.full_rows, d.counts + 3);
             launch_accum_rows(ds, d.full_rows, d.counts + 3);
             launch_bc_rows_list(ds, +1, d.full_rows, d.counts + 3);
             CK(g, cudaEventRecord(g->ev_join, g->side));

@@ -216,7 +216,7 @@ struct Dev {
 };
 
 constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction
-constexpr int kAccThreads = 512;
+constexpr int kAccThreads = 1024;
 
 // Accumulation launch shape for n and the current E* capacity (sets acc_grid, acc_smem,
 // acc_mask_smem and ws_stride of d); the work space must then hold acc_grid * ws_stride.

@@ -131,7 +131,7 @@ static size_t smem_base(int n) {
 }
 static size_t mask_bytes(int64_t cap) { return 4 * (size_t)((cap + 31) / 32); }
 
-constexpr size_t kSmemLimit = 200 * 1024;
+constexpr size_t kSmemLimit = 180 * 1024;
 
 void accum_config(Dev& d) {
     const size_t base = smem_base(d.n);

@@ -343,7 +343,7 @@ void batch_config(BatchLaunch& L, int dbytes, int n_max, int64_t cap_max) {
     const size_t np = ((size_t)n_max + 31) & ~(size_t)31;
     const size_t base = 4 * np + 2 * (size_t)kBigCap;
     const size_t mb = 4 * (size_t)((cap_max + 31) / 32);
-    const size_t limit = 200 * 1024;
+    const size_t limit = 180 * 1024;
     L.mask_in_smem = base + mb <= limit ? 1 : 0;
     L.acc_smem = (int)(L.mask_in_smem ? base + mb : base);
     int per_sm = 1;
