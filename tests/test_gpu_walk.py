@@ -154,3 +154,18 @@ def test_walk_option_rejected_on_directed_graphs():
     with pytest.raises(binding.BCError) as e:
         a.bc_set_option("pair_walk", 1)
     assert e.value.code == binding.BC_ERR_ARG
+
+
+def test_walk_through_hubs():
+    # hubs with hundreds of E* arcs on the walks of many rows, and a vertex update of the
+    # largest hub: results must equal the column test's bit for bit
+    g = synth.barabasi_albert(3000, 4, 1, 3, 3003)
+    deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n)
+    assert deg.max() >= 64
+    hub = int(np.argmax(deg))
+    ups = synth.update_stream(g, 4, 4, 4, 3004, 1, 3, kmin=2, kmax=6)
+    em = synth.EdgeMap.of(synth.apply_updates(g, ups))
+    far = [x for x in range(g.n - 1, 0, -1) if x != hub and em.get(x, hub) is None][:6]
+    ups.append(("vertex", hub, [(x, 1, 0) for x in far]))
+    info = _walk_vs_test(g, ups, "i32", "BA n=3000 hubs", every=4)
+    assert info["walk_pairs"] > 0
