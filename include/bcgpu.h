@@ -357,7 +357,10 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
 /* bc_batch_set_tiles -- launch shape of the batch kernels (what the autotuner varies):
  * tiles[0] CTAs per SM of the per-vertex passes (1..64), tiles[1] of the rank-1 pass,
  * tiles[2] of the BC row sums, tiles[3] cap on accumulation CTAs per SM (0 = as many as
- * fit).  The next bc_batch_apply captures a new CUDA graph. */
+ * fit); with count >= 6 also the rank-1 pass's tile and schedule: tiles[4] 16-byte
+ * vectors per thread per work item (1, 2, 4 or 8: the item's column chunk is 256
+ * threads x tiles[4] x 16 bytes), tiles[5] 0 = a contiguous block of items per CTA,
+ * 1 = items dealt out to the CTAs in turn.  The next bc_batch_apply captures a new CUDA graph. */
 int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count);
 
 /* bc_batch_last_ms -- device time (CUDA events around the graph launch) of the last apply. */

@@ -1,7 +1,9 @@
 """Autotuner for the launch shape of batches of graphs (bc_batch_set_tiles).
 
 The tunable shape is (CTAs per SM of the per-vertex passes, of the rank-1 pass, of the
-BC row sums, cap on accumulation CTAs per SM).  The tuner runs coordinate descent from a
+BC row sums, cap on accumulation CTAs per SM, the rank-1 pass's tile -- 16-byte vectors
+per thread per work item, so its column chunk -- and its schedule -- contiguous item
+blocks per CTA or items dealt out in turn).  The tuner runs coordinate descent from a
 default: for each parameter in turn it applies one batch step with every candidate value
 (each step consumes the next updates of the caller's stream, so the graphs advance as
 they would anyway) and keeps the fastest.  Results are cached in
@@ -15,8 +17,8 @@ import os
 
 from . import build as _build
 
-DEFAULT = [4, 8, 8, 0]
-CANDIDATES = [[2, 4, 8], [4, 8, 16], [4, 8, 16], [0, 1]]
+DEFAULT = [4, 8, 8, 0, 4, 0]
+CANDIDATES = [[2, 4, 8], [4, 8, 16], [4, 8, 16], [0, 1], [1, 2, 4, 8], [0, 1]]
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 
 
@@ -50,7 +52,7 @@ def tune(batch, next_step, key: str | None = None, use_cache: bool = True):
     lists of the next step.  Returns (tiles, trials) where trials lists (tiles, ms)."""
     if use_cache and key is not None:
         cached = load_cache().get(key)
-        if cached:
+        if cached and len(cached) == len(DEFAULT):
             batch.bc_batch_set_tiles(cached)
             return cached, []
     best = list(DEFAULT)

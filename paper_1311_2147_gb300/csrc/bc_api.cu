@@ -1313,6 +1313,8 @@ int bc_batch_create(bc_batch** out, int32_t count, bc_graph* const* graphs, void
     b->L.scan_ctas = 8;
     b->L.bc_ctas = 8;
     b->L.acc_per_sm = 0;
+    b->L.scan_unroll = 4;   // the single-graph item width (kScanUnroll)
+    b->L.scan_sched = 0;
     int rc;
     if ((rc = balloc(b, &b->d_devs, count)) || (rc = balloc(b, &b->d_coff, count + 1)) ||
         (rc = balloc(b, &b->d_plans, 3 * ((size_t)count + 1)))) {
@@ -1336,10 +1338,17 @@ int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count) {
     for (int i = 0; i < 4; ++i)
         if (tiles[i] < 0 || tiles[i] > 64) return bfail(b, BC_ERR_ARG, "tile value out of range");
     if (tiles[0] < 1 || tiles[1] < 1 || tiles[2] < 1) return bfail(b, BC_ERR_ARG, "tile value out of range");
+    if (count >= 6 && ((tiles[4] != 1 && tiles[4] != 2 && tiles[4] != 4 && tiles[4] != 8) ||
+                       (tiles[5] != 0 && tiles[5] != 1)))
+        return bfail(b, BC_ERR_ARG, "rank-1 chunk (1, 2, 4, 8) or schedule (0, 1) out of range");
     b->L.vpass_ctas = tiles[0];
     b->L.scan_ctas = tiles[1];
     b->L.bc_ctas = tiles[2];
     b->L.acc_per_sm = tiles[3];
+    if (count >= 6) {
+        b->L.scan_unroll = tiles[4];
+        b->L.scan_sched = tiles[5];
+    }
     b->cap_max = -1;   // forces a new launch configuration
     drop_exec(b);
     return BC_OK;

@@ -47,6 +47,10 @@ struct BatchLaunch {
     int32_t scan_ctas;    // CTAs per SM of the rank-1 pass             (tunable)
     int32_t bc_ctas;      // CTAs per SM of the BC row sums             (tunable)
     int32_t acc_per_sm;   // cap on accumulation CTAs per SM, 0 = max   (tunable)
+    int32_t scan_unroll;  // 16-byte vectors per thread per rank-1 item: the item's column
+                          // chunk is 256 threads x this x the vector width (1, 2, 4, 8; tunable)
+    int32_t scan_sched;   // 0: a contiguous block of items per CTA; 1: items dealt out in
+                          // turn (item = CTA + k * grid)                (tunable)
     int32_t acc_grid;
     int32_t acc_smem;
     int32_t mask_in_smem;

@@ -498,12 +498,12 @@ __device__ __forceinline__ bool scan_vec(const ScanArgs<DT>& a, int s, size_t ro
 }
 
 // One work item of the rank-1 pass: row s (scalars rd, rs, rm), chunk c of CW columns.
-template <typename DT, bool VECTOR>
+template <typename DT, bool VECTOR, int U = kScanUnroll>
 __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int64_t rd, uint64_t rs, uint64_t rm,
                                               int c, int& n_changed, int& n_ties) {
     using V = Vec<DT>;
     constexpr int VN = V::N;
-    constexpr int CW = kScanThreads * VN * kScanUnroll;
+    constexpr int CW = kScanThreads * VN * U;
     const int n = a.n;
     const int64_t INF = Inf<DT>::v;
     const size_t rowoff = (size_t)s * n;
@@ -511,9 +511,9 @@ __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int6
     const int t0 = c * CW;
     const int tid = threadIdx.x % kScanThreads;
     if constexpr (VECTOR) {
-        typename V::T dv[kScanUnroll], cv[kScanUnroll];
+        typename V::T dv[U], cv[U];
 #pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int t = t0 + (u * kScanThreads + tid) * VN;
             if (t < n) {
                 dv[u] = __ldcs(reinterpret_cast<const typename V::T*>(Drow + t));
@@ -521,7 +521,7 @@ __device__ __forceinline__ void dev_scan_item(const ScanArgs<DT>& a, int s, int6
             }
         }
 #pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int t = t0 + (u * kScanThreads + tid) * VN;
             if (t >= n) break;
             if (scan_vec<DT>(a, s, rowoff, t, dv[u], cv[u], rd, rs, rm, n_changed, n_ties))
@@ -684,9 +684,10 @@ __device__ __forceinline__ int select_bit(const uint32_t* m, int beg, int r) {
 }
 
 // Exclusive block-wide prefix sum of v (all threads call it); *total gets the sum.
-// s_ws needs kAccThreads / 32 + 1 ints and must not be reused before a barrier.
+// s_ws needs T / 32 + 1 ints and must not be reused before a barrier (T threads).
+template <int T>
 __device__ __forceinline__ int block_excl_scan(int v, int* s_ws, int* total) {
-    constexpr int NW = kAccThreads / 32;
+    constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int incl = v;
 #pragma unroll
@@ -712,9 +713,10 @@ __device__ __forceinline__ int block_excl_scan(int v, int* s_ws, int* total) {
     return s_ws[warp] + incl - v;
 }
 
-// Last index i in [0, kAccThreads) with off[i] <= j (off non-decreasing, off[0] = 0).
+// Last index i in [0, T) with off[i] <= j (off non-decreasing, off[0] = 0).
+template <int T>
 __device__ __forceinline__ int owner_of(const int* off, int j) {
-    int lo = 0, hi = kAccThreads;
+    int lo = 0, hi = T;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (off[mid] <= j) lo = mid;
@@ -752,22 +754,23 @@ __device__ __forceinline__ void push_sigma(uint64_t* Ss, int b, uint64_t sx, int
 // A round of a level pass gives every thread up to kPerThread vertices of the level.
 constexpr int kPerThread = 2;
 
+template <int T>
 struct LevelSmem {
-    int off[kAccThreads];                  // first arc rank of the thread's vertices
-    int beg[kPerThread][kAccThreads];      // slot range start of each vertex
-    int k0[kAccThreads];                   // DAG out-arcs of the thread's first vertex
-    uint64_t sx[kPerThread][kAccThreads];  // path counts (static pass 2)
-    ff buf[kAccThreads];
-    int ws[kAccThreads / 32 + 1];
+    int off[T];                  // first arc rank of the thread's vertices
+    int beg[kPerThread][T];      // slot range start of each vertex
+    int k0[T];                   // DAG out-arcs of the thread's first vertex
+    uint64_t sx[kPerThread][T];  // path counts (static pass 2)
+    ff buf[T];
+    int ws[T / 32 + 1];
 };
 
-template <typename DT, bool STATIC, typename DA>
+template <typename DT, bool STATIC, int T, typename DA>
 __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA dist, int s, uint64_t* Ss,
                                                   ff* out, uint32_t* cnt, uint16_t* order, uint32_t* mask,
-                                                  uint16_t* big, LevelSmem& ls, ff* rho, int32_t* lvl,
+                                                  uint16_t* big, LevelSmem<T>& ls, ff* rho, int32_t* lvl,
                                                   int* s_tail, int* s_nbig) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int T = kAccThreads, NW = kAccThreads / 32, U = 8;
+    constexpr int NW = T / 32, U = 8;
     // ---- pass 1: DAG'(s) membership of every slot, and in-degrees (loads of U chunks
     // are issued before any of them is used)
     const int nchunk = (int)((a.e_cap + 31) >> 5);
@@ -831,7 +834,7 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                 if (STATIC) ls.sx[v][tid] = k ? Ss[x] : 0ull;
             }
             int total;
-            const int off = block_excl_scan(kt, ls.ws, &total);
+            const int off = block_excl_scan<T>(kt, ls.ws, &total);
             ls.off[tid] = off;
             ls.k0[tid] = kk[0];
             __syncthreads();
@@ -840,7 +843,7 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                 bool ready = false;
                 int b = 0;
                 if (j < total) {
-                    const int o = owner_of(ls.off, j);
+                    const int o = owner_of<T>(ls.off, j);
                     int r = j - ls.off[o];
                     const int v = r < ls.k0[o] ? 0 : 1;
                     if (v) r -= ls.k0[o];
@@ -906,7 +909,7 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
                 ls.beg[v][tid] = beg;
             }
             int total;
-            const int off = block_excl_scan(kt, ls.ws, &total);
+            const int off = block_excl_scan<T>(kt, ls.ws, &total);
             ls.off[tid] = off;
             ls.k0[tid] = kk[0];
             __syncthreads();
@@ -916,7 +919,7 @@ __device__ __forceinline__ void accumulate_source(const AccArgs<DT>& a, const DA
             for (int jb = 0; jb < total; jb += T) {
                 const int j = jb + tid;
                 if (j < total) {
-                    const int o = owner_of(ls.off, j);
+                    const int o = owner_of<T>(ls.off, j);
                     int r = j - ls.off[o];
                     const int v = r < ls.k0[o] ? 0 : 1;
                     if (v) r -= ls.k0[o];
@@ -987,8 +990,8 @@ __device__ __forceinline__ AccSmem acc_smem(const AccArgs<DT>& a, unsigned char*
 // Re-accumulate source s (whole block; every thread calls it): stage its distance row,
 // rebuild DAG'(s), order it, pull Eq. 4, write its delta row (and, statically, its
 // sigma row).
-template <typename DT, bool STATIC>
-__device__ __forceinline__ void dev_accum_source(const AccArgs<DT>& a, int s, const AccSmem& m, LevelSmem& ls,
+template <typename DT, bool STATIC, int T>
+__device__ __forceinline__ void dev_accum_source(const AccArgs<DT>& a, int s, const AccSmem& m, LevelSmem<T>& ls,
                                                  int* s_tail, int* s_nbig) {
     const int n = a.n;
     const int np = (n + 31) & ~31;
@@ -998,7 +1001,7 @@ __device__ __forceinline__ void dev_accum_source(const AccArgs<DT>& a, int s, co
     uint64_t* Ss = a.S + (size_t)s * n;
     ff* out = a.Dl + (size_t)s * n;
     int wide = 0;
-    for (int t = tid; t < n; t += kAccThreads) {
+    for (int t = tid; t < n; t += T) {
         const int64_t v = Ds[t];
         uint16_t c;
         if (v == INF) c = 0xFFFF;
@@ -1008,13 +1011,13 @@ __device__ __forceinline__ void dev_accum_source(const AccArgs<DT>& a, int s, co
         out[t] = ff{0.0f, 0.0f};
         if (STATIC) Ss[t] = (t == s) ? 1ull : 0ull;
     }
-    for (int t = tid; t < np / 2; t += kAccThreads) m.cnt[t] = 0u;
+    for (int t = tid; t < np / 2; t += T) m.cnt[t] = 0u;
     wide = __syncthreads_or(wide);
     if (!wide)
-        accumulate_source<DT, STATIC>(a, Dist16{m.d16}, s, Ss, out, m.cnt, m.order, m.mask, m.big, ls, m.rho, m.lvl,
+        accumulate_source<DT, STATIC, T>(a, Dist16{m.d16}, s, Ss, out, m.cnt, m.order, m.mask, m.big, ls, m.rho, m.lvl,
                                       s_tail, s_nbig);
     else
-        accumulate_source<DT, STATIC>(a, DistG<DT>{Ds}, s, Ss, out, m.cnt, m.order, m.mask, m.big, ls, m.rho, m.lvl,
+        accumulate_source<DT, STATIC, T>(a, DistG<DT>{Ds}, s, Ss, out, m.cnt, m.order, m.mask, m.big, ls, m.rho, m.lvl,
                                       s_tail, s_nbig);
     __syncthreads();
 }

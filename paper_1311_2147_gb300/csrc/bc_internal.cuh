@@ -185,6 +185,7 @@ struct Dev {
     int32_t acc_grid;    // CTAs of the accumulation kernel
     int32_t acc_smem;    // dynamic shared memory of the accumulation kernel
     int32_t acc_mask_smem;  // 1: the DAG slot mask lives in shared memory
+    int32_t acc_threads;    // threads of an accumulation CTA (kAccThreadsWide or kAccThreadsNarrow)
     int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
     int64_t ws_stride;
     // pair-dependency corrections (undirected graphs): the pairs changed by this update,
@@ -216,7 +217,12 @@ struct Dev {
 };
 
 constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction
-constexpr int kAccThreads = 1024;
+// Threads of an accumulation CTA (one source at a time): 1024 for graphs of at least
+// kAccWideMinN vertices (the level passes of one source spread over more threads), 512
+// otherwise (more sources in flight per SM); the batched path uses 512.
+constexpr int kAccThreadsWide = 1024;
+constexpr int kAccThreadsNarrow = 512;
+constexpr int kAccWideMinN = 4096;
 
 // Accumulation launch shape for n and the current E* capacity (sets acc_grid, acc_smem,
 // acc_mask_smem and ws_stride of d); the work space must then hold acc_grid * ws_stride.

@@ -37,16 +37,16 @@ namespace bcg {
 
 // One CTA per source at a time (shared memory as described at AccSmem; the per-round
 // scratch of the level passes is static shared memory).
-template <typename DT, bool STATIC>
-__global__ void __launch_bounds__(kAccThreads) k_accum_smem(AccArgs<DT> a) {
+template <typename DT, bool STATIC, int T>
+__global__ void __launch_bounds__(T, 1) k_accum_smem(AccArgs<DT> a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ LevelSmem ls;
+    __shared__ LevelSmem<T> ls;
     __shared__ int s_tail, s_nbig;
     const AccSmem m = acc_smem(a, smem, a.ws + (size_t)blockIdx.x * a.ws_stride);
     const int total = STATIC ? a.n : *a.count;
     for (int i = blockIdx.x; i < total; i += gridDim.x) {
         if (block_err(a.err)) return;
-        dev_accum_source<DT, STATIC>(a, STATIC ? i : a.rows[i], m, ls, &s_tail, &s_nbig);
+        dev_accum_source<DT, STATIC, T>(a, STATIC ? i : a.rows[i], m, ls, &s_tail, &s_nbig);
     }
 }
 
@@ -133,22 +133,27 @@ static size_t mask_bytes(int64_t cap) { return 4 * (size_t)((cap + 31) / 32); }
 
 constexpr size_t kSmemLimit = 180 * 1024;
 
+template <typename DT, int T>
+static int accum_occupancy(size_t smem) {
+    const int maxs = (int)kSmemLimit;
+    cudaFuncSetAttribute(k_accum_smem<DT, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    cudaFuncSetAttribute(k_accum_smem<DT, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_accum_smem<DT, false, T>, T, smem);
+    return per_sm;
+}
+
 void accum_config(Dev& d) {
     const size_t base = smem_base(d.n);
     const size_t mb = mask_bytes(d.e_cap);
     const bool in_smem = base + mb <= kSmemLimit;
     const size_t smem = in_smem ? base + mb : base;
-    int per_sm = 1;
-    const int maxs = (int)kSmemLimit;
-    if (d.dbytes == 4) {
-        cudaFuncSetAttribute(k_accum_smem<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-        cudaFuncSetAttribute(k_accum_smem<int32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_accum_smem<int32_t, false>, kAccThreads, smem);
-    } else {
-        cudaFuncSetAttribute(k_accum_smem<int64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-        cudaFuncSetAttribute(k_accum_smem<int64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_accum_smem<int64_t, false>, kAccThreads, smem);
-    }
+    d.acc_threads = d.n >= kAccWideMinN ? kAccThreadsWide : kAccThreadsNarrow;
+    const bool wide = d.acc_threads == kAccThreadsWide;
+    int per_sm = d.dbytes == 4 ? (wide ? accum_occupancy<int32_t, kAccThreadsWide>(smem)
+                                       : accum_occupancy<int32_t, kAccThreadsNarrow>(smem))
+                               : (wide ? accum_occupancy<int64_t, kAccThreadsWide>(smem)
+                                       : accum_occupancy<int64_t, kAccThreadsNarrow>(smem));
     if (per_sm < 1) per_sm = 1;
     d.acc_smem = (int32_t)smem;
     d.acc_mask_smem = in_smem ? 1 : 0;
@@ -159,15 +164,22 @@ void accum_config(Dev& d) {
 }
 
 // Algorithm 1 for the sources listed in rows[0..*count), or for every source.
-static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
+template <typename DT, int T>
+static void accum_t(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
     const int grid = d.acc_grid;
     const size_t smem = (size_t)d.acc_smem;
+    if (is_static) k_accum_smem<DT, true, T><<<grid, T, smem, d.st>>>(acc_args<DT>(d, rows, count));
+    else k_accum_smem<DT, false, T><<<grid, T, smem, d.st>>>(acc_args<DT>(d, rows, count));
+}
+
+static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
+    const bool wide = d.acc_threads == kAccThreadsWide;
     if (d.dbytes == 4) {
-        if (is_static) k_accum_smem<int32_t, true><<<grid, kAccThreads, smem, d.st>>>(acc_args<int32_t>(d, rows, count));
-        else k_accum_smem<int32_t, false><<<grid, kAccThreads, smem, d.st>>>(acc_args<int32_t>(d, rows, count));
+        if (wide) accum_t<int32_t, kAccThreadsWide>(d, is_static, rows, count);
+        else accum_t<int32_t, kAccThreadsNarrow>(d, is_static, rows, count);
     } else {
-        if (is_static) k_accum_smem<int64_t, true><<<grid, kAccThreads, smem, d.st>>>(acc_args<int64_t>(d, rows, count));
-        else k_accum_smem<int64_t, false><<<grid, kAccThreads, smem, d.st>>>(acc_args<int64_t>(d, rows, count));
+        if (wide) accum_t<int64_t, kAccThreadsWide>(d, is_static, rows, count);
+        else accum_t<int64_t, kAccThreadsNarrow>(d, is_static, rows, count);
     }
 }
 

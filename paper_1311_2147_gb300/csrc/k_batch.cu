@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kCompactThreads) kb_compact(BatchArgs b, int r
 // kind 0: scan items of the phase rows (rows x column chunks); 1: BC partial tasks
 // (column blocks x row blocks of the rows to re-accumulate); 2: sources to
 // re-accumulate.  One CTA.
-__global__ void __launch_bounds__(1024) kb_plan(BatchArgs b, int r, int kind, int phase_active, int64_t* out) {
+__global__ void __launch_bounds__(1024) kb_plan(BatchArgs b, int r, int kind, int phase_active, int64_t* out,
+                                                int scan_unroll) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total, s_base;
     const int G = b.G, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(1024) kb_plan(BatchArgs b, int r, int kind, in
             const bool on = (phase_active == 0) ? (u.kin != 0) : (phase_active == 1) ? (u.kout != 0) : (u.present != 0);
             if (on && *d.err == 0) {
                 if (kind == 0) {
-                    const int cw = kScanThreads * (d.dbytes == 4 ? 4 : 2) * kScanUnroll;
+                    const int cw = kScanThreads * (d.dbytes == 4 ? 4 : 2) * scan_unroll;
                     v = (int64_t)d.counts[0] * ((d.n + cw - 1) / cw);
                     atomicAdd(reinterpret_cast<unsigned long long*>(d.stats + 6), (unsigned long long)d.counts[0]);
                 } else if (kind == 1) {
@@ -195,21 +196,25 @@ __device__ __forceinline__ ScanArgs<DT> batch_scan_args(const Dev& d, const Batc
     return a;
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(kScanThreads, 4) kb_scan(BatchArgs b, int r, int phase, const int64_t* off) {
+// U: vectors per thread per item (the item's chunk width); sched 0: a contiguous block of
+// items per CTA, 1: items dealt out in turn.
+template <typename DT, int U>
+__global__ void __launch_bounds__(kScanThreads, 4) kb_scan(BatchArgs b, int r, int phase, const int64_t* off,
+                                                           int sched) {
     const int G = b.G;
     const int64_t total = off[G];
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const int64_t it0 = (int64_t)blockIdx.x * per;
-    const int64_t it1 = min(total, it0 + per);
+    const int64_t it0 = sched ? (int64_t)blockIdx.x : (int64_t)blockIdx.x * per;
+    const int64_t it1 = sched ? total : min(total, it0 + per);
+    const int64_t step = sched ? (int64_t)gridDim.x : 1;
     constexpr int VN = Vec<DT>::N;
-    constexpr int CW = kScanThreads * VN * kScanUnroll;
+    constexpr int CW = kScanThreads * VN * U;
     int cg = -1, cur = -1, s = -1, nchunks = 1;
     int64_t rd = Inf<DT>::v;
     uint64_t rs = 0, rm = 0;
     int n_changed = 0, n_ties = 0;
     ScanArgs<DT> a{};
-    for (int64_t j = it0; j < it1; ++j) {
+    for (int64_t j = it0; j < it1; j += step) {
         int g = cg;
         if (g < 0 || j >= off[g + 1] || j < off[g]) {
             // flush the counters of the previous graph before moving on
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) kb_scan(BatchArgs b, int r, i
             rm = a.fM[s];
         }
         if (rd == Inf<DT>::v) continue;
-        if (a.n % VN == 0) dev_scan_item<DT, true>(a, s, rd, rs, rm, c, n_changed, n_ties);
-        else dev_scan_item<DT, false>(a, s, rd, rs, rm, c, n_changed, n_ties);
+        if (a.n % VN == 0) dev_scan_item<DT, true, U>(a, s, rd, rs, rm, c, n_changed, n_ties);
+        else dev_scan_item<DT, false, U>(a, s, rd, rs, rm, c, n_changed, n_ties);
     }
     if (cg >= 0) scan_stats(a.stats, n_changed, n_ties);
     else scan_stats(b.devs[0].stats, 0, 0);
@@ -276,9 +281,9 @@ __global__ void kb_bc_finish(BatchArgs b, int r, double sign) {
 // ---------------------------------------------------------------- accumulation
 
 template <typename DT>
-__global__ void __launch_bounds__(kAccThreads) kb_accum(BatchArgs b, int r, const int64_t* off) {
+__global__ void __launch_bounds__(kAccThreadsNarrow) kb_accum(BatchArgs b, int r, const int64_t* off) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ LevelSmem ls;
+    __shared__ LevelSmem<kAccThreadsNarrow> ls;
     __shared__ int s_tail, s_nbig;
     const int G = b.G;
     const int64_t total = off[G];
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kAccThreads) kb_accum(BatchArgs b, int r, cons
         a.err = d.err;
         a.mask_in_smem = b.mask_in_smem;
         const AccSmem m = acc_smem(a, smem, wsb);
-        dev_accum_source<DT, false>(a, d.acc_rows[j - off[g]], m, ls, &s_tail, &s_nbig);
+        dev_accum_source<DT, false, kAccThreadsNarrow>(a, d.acc_rows[j - off[g]], m, ls, &s_tail, &s_nbig);
     }
 }
 
@@ -313,28 +318,39 @@ __global__ void __launch_bounds__(kAccThreads) kb_accum(BatchArgs b, int r, cons
 static inline int nb(int64_t x, int t) { return (int)std::max<int64_t>(1, (x + t - 1) / t); }
 
 template <typename DT>
+static void batch_scan(const BatchArgs& b, const BatchLaunch& L, int r, int phase, cudaStream_t st) {
+    const int grid = L.nsm * L.scan_ctas;
+    switch (L.scan_unroll) {
+        case 1: kb_scan<DT, 1><<<grid, kScanThreads, 0, st>>>(b, r, phase, b.plan_scan, L.scan_sched); break;
+        case 2: kb_scan<DT, 2><<<grid, kScanThreads, 0, st>>>(b, r, phase, b.plan_scan, L.scan_sched); break;
+        case 8: kb_scan<DT, 8><<<grid, kScanThreads, 0, st>>>(b, r, phase, b.plan_scan, L.scan_sched); break;
+        default: kb_scan<DT, 4><<<grid, kScanThreads, 0, st>>>(b, r, phase, b.plan_scan, L.scan_sched); break;
+    }
+}
+
+template <typename DT>
 static void round_launches(const BatchArgs& b, const BatchLaunch& L, int r, cudaStream_t st) {
     const int nsm = L.nsm;
     kb_estar<<<nb(L.max_eops, 256), 256, 0, st>>>(b, r);
     // IN phase
     kb_vertex_pass<DT><<<nsm * L.vpass_ctas, 256, 0, st>>>(b, r, 0);
     kb_compact<<<std::min(b.G, nsm * 2), kCompactThreads, 0, st>>>(b, r, 0);
-    kb_plan<<<1, 1024, 0, st>>>(b, r, 0, 0, b.plan_scan);
-    kb_scan<DT><<<nsm * L.scan_ctas, kScanThreads, 0, st>>>(b, r, 0, b.plan_scan);
+    kb_plan<<<1, 1024, 0, st>>>(b, r, 0, 0, b.plan_scan, L.scan_unroll);
+    batch_scan<DT>(b, L, r, 0, st);
     // OUT phase (graphs without out-edges in this round have no work)
     kb_vertex_pass<DT><<<nsm * L.vpass_ctas, 256, 0, st>>>(b, r, 2);
     kb_vertex_pass<DT><<<nsm * L.vpass_ctas, 256, 0, st>>>(b, r, 1);
     kb_compact<<<std::min(b.G, nsm * 2), kCompactThreads, 0, st>>>(b, r, 1);
-    kb_plan<<<1, 1024, 0, st>>>(b, r, 0, 1, b.plan_scan);
-    kb_scan<DT><<<nsm * L.scan_ctas, kScanThreads, 0, st>>>(b, r, 1, b.plan_scan);
+    kb_plan<<<1, 1024, 0, st>>>(b, r, 0, 1, b.plan_scan, L.scan_unroll);
+    batch_scan<DT>(b, L, r, 1, st);
     kb_vertex_pass<DT><<<nsm * L.vpass_ctas, 256, 0, st>>>(b, r, 3);
     // rows to re-accumulate, BC minus the old rows, accumulation, BC plus the new rows
     kb_compact<<<std::min(b.G, nsm * 2), kCompactThreads, 0, st>>>(b, r, 2);
-    kb_plan<<<1, 1024, 0, st>>>(b, r, 1, 2, b.plan_bc);
-    kb_plan<<<1, 1024, 0, st>>>(b, r, 2, 2, b.plan_acc);
+    kb_plan<<<1, 1024, 0, st>>>(b, r, 1, 2, b.plan_bc, L.scan_unroll);
+    kb_plan<<<1, 1024, 0, st>>>(b, r, 2, 2, b.plan_acc, L.scan_unroll);
     kb_bc_partial<<<nsm * L.bc_ctas, 256, 0, st>>>(b, r, b.plan_bc);
     kb_bc_finish<<<nsm * 2, 256, 0, st>>>(b, r, -1.0);
-    kb_accum<DT><<<L.acc_grid, kAccThreads, L.acc_smem, st>>>(b, r, b.plan_acc);
+    kb_accum<DT><<<L.acc_grid, kAccThreadsNarrow, L.acc_smem, st>>>(b, r, b.plan_acc);
     kb_bc_partial<<<nsm * L.bc_ctas, 256, 0, st>>>(b, r, b.plan_bc);
     kb_bc_finish<<<nsm * 2, 256, 0, st>>>(b, r, +1.0);
 }
@@ -349,10 +365,10 @@ void batch_config(BatchLaunch& L, int dbytes, int n_max, int64_t cap_max) {
     int per_sm = 1;
     if (dbytes == 4) {
         cudaFuncSetAttribute(kb_accum<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_accum<int32_t>, kAccThreads, L.acc_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_accum<int32_t>, kAccThreadsNarrow, L.acc_smem);
     } else {
         cudaFuncSetAttribute(kb_accum<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_accum<int64_t>, kAccThreads, L.acc_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_accum<int64_t>, kAccThreadsNarrow, L.acc_smem);
     }
     if (per_sm < 1) per_sm = 1;
     if (L.acc_per_sm > 0) per_sm = std::min(per_sm, L.acc_per_sm);

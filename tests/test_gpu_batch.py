@@ -90,15 +90,16 @@ def test_batch_stops_a_graph_at_its_invalid_update():
 def test_batch_tiles_do_not_change_results():
     fam = _family(6, 33, nlo=50, nhi=200)
     outs = []
-    for tiles in ([4, 8, 8, 0], [1, 2, 1, 1]):
+    for tiles in ([4, 8, 8, 0], [1, 2, 1, 1], [4, 8, 8, 0, 1, 0], [4, 8, 8, 0, 8, 1], [2, 4, 4, 1, 2, 1]):
         graphs = [binding.BCGraph(g) for g, _ in fam]
         batch = binding.BCBatch(graphs)
         batch.bc_batch_set_tiles(tiles)
         rc, _ = batch.bc_batch_apply([ups for _, ups in fam])
         assert rc == 0
         outs.append([m.bc_get_scores() for m in graphs])
-    for a, b in zip(*outs):
-        assert np.array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
 
 
 def test_batch_config_shape_sample():

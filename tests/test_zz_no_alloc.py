@@ -11,6 +11,8 @@ bc_init_static + bc_get_scores and with the oracle within the parity tolerance; 
 repeated call must leave the device's free memory unchanged.  This file is collected
 last so that a run stopping at the first failure has run every other test first.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -89,13 +91,21 @@ def test_noalloc_second_call_allocates_nothing():
         assert rc == binding.BC_OK
         t_off, t_dst, t_w, t_out = _device_inputs(torch, g)
         stream = torch.cuda.current_stream().cuda_stream
-        free0, _ = torch.cuda.mem_get_info()
-        alloc0 = torch.cuda.memory_allocated()
-        rc = lib.bc_static_scores_noalloc(g.n, int(t_dst.shape[0]), t_off.data_ptr(), t_dst.data_ptr(),
-                                          t_w.data_ptr(), flags, t_out.data_ptr(), stream)
+        # handles of earlier tests freed by the garbage collector inside the window would
+        # raise the free memory: collect them first and keep the collector off meanwhile
+        gc.collect()
         torch.cuda.synchronize()
-        free1, _ = torch.cuda.mem_get_info()
-        alloc1 = torch.cuda.memory_allocated()
+        gc.disable()
+        try:
+            free0, _ = torch.cuda.mem_get_info()
+            alloc0 = torch.cuda.memory_allocated()
+            rc = lib.bc_static_scores_noalloc(g.n, int(t_dst.shape[0]), t_off.data_ptr(), t_dst.data_ptr(),
+                                              t_w.data_ptr(), flags, t_out.data_ptr(), stream)
+            torch.cuda.synchronize()
+            free1, _ = torch.cuda.mem_get_info()
+            alloc1 = torch.cuda.memory_allocated()
+        finally:
+            gc.enable()
         assert rc == binding.BC_OK
         assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
         assert alloc1 == alloc0
