@@ -592,7 +592,7 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     binding.load()
     W, K, per = args.warmup, args.steps, 8
-    tune_steps = 2 * (1 + sum(len(c) - 1 for c in autotune.CANDIDATES))
+    tune_steps = autotune.steps_needed()
     total_steps = tune_steps + W + K
     t0 = time.perf_counter()
     fam = synth.workload_batch(count=args.batch_graphs, n_updates=per, rounds=total_steps)
@@ -723,6 +723,13 @@ def run_serve(args):
                          "failures": int((res["status"] != 0).sum())})
     head = min(runs, key=lambda r: abs(r["load"] - 0.8))
     st = srv.stats()
+    # counters summed over the resident graphs (what explains the latency tail: updates
+    # that re-accumulate many rows, E* segment moves and re-layouts)
+    counters = {}
+    for gid in gids:
+        info = srv.graph(gid).bc_get_info()
+        for k in ("updates_applied", "noop_updates", "rows_full", "estar_moves", "estar_rebuilds", "max_rows"):
+            counters[k] = max(counters.get(k, 0), info[k]) if k == "max_rows" else counters.get(k, 0) + info[k]
     line = {"metric": "serving: updates/sec and p50/p99 latency over resident graphs",
             "value": head["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": head["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -734,7 +741,7 @@ def run_serve(args):
             "latency_ms": head["latency_ms"], "loads": runs,
             "closed_loop_failures": int((res_c["status"] != 0).sum()),
             "open_loop_failures": sum(r["failures"] for r in runs),
-            "server": st, "clocks": clk.summary()}
+            "server": st, "graph_counters": counters, "clocks": clk.summary()}
     print(json.dumps(line))
     return 0
 

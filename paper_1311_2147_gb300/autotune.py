@@ -20,6 +20,12 @@ from . import build as _build
 DEFAULT = [4, 8, 8, 0, 4, 0]
 CANDIDATES = [[2, 4, 8], [4, 8, 16], [4, 8, 16], [0, 1], [1, 2, 4, 8], [0, 1]]
 CACHE = os.path.join(_build.BUILD, "autotune.json")
+TIMED_STEPS = 2   # timed batch steps per candidate (after one untimed step that captures the graph)
+
+
+def steps_needed() -> int:
+    """Batch steps one tuning run consumes."""
+    return (1 + TIMED_STEPS) * (1 + sum(len(c) - 1 for c in CANDIDATES))
 
 
 def cache_key(count: int, n_max: int, dist: str) -> str:
@@ -63,10 +69,12 @@ def tune(batch, next_step, key: str | None = None, use_cache: bool = True):
         rc, _ = batch.bc_batch_apply(next_step())   # captures a new CUDA graph, untimed
         if rc != 0:
             raise RuntimeError(f"batch step failed during tuning: {rc} {batch.last_error()}")
-        rc, _ = batch.bc_batch_apply(next_step())
-        if rc != 0:
-            raise RuntimeError(f"batch step failed during tuning: {rc} {batch.last_error()}")
-        ms = batch.bc_batch_last_ms()
+        ms = 0.0
+        for _ in range(TIMED_STEPS):   # steps differ in work: more than one evens that out
+            rc, _ = batch.bc_batch_apply(next_step())
+            if rc != 0:
+                raise RuntimeError(f"batch step failed during tuning: {rc} {batch.last_error()}")
+            ms += batch.bc_batch_last_ms()
         trials.append((list(tiles), ms))
         return ms
 
