@@ -260,6 +260,33 @@ __device__ __forceinline__ void record_change(const PairRec& r, int n, int s, in
     if (pos < r.tcap) r.tlist[(size_t)s * r.tcap + pos] = t;
 }
 
+// ---- programmatic dependent launch ----
+// The kernels of an update run one after another on the handle's stream.  They are
+// launched with programmatic stream serialization allowed, so the launch of the next
+// kernel is processed while this one runs, and each one starts with pdl_enter(): a wait
+// for the previous kernel's completion and memory before touching any data.  No kernel
+// triggers its dependents early: the next kernel's CTAs are placed only as this grid's
+// CTAs exit (an early trigger let every later kernel's CTAs occupy SMs while waiting,
+// which slowed the running kernel).  Launched the ordinary way, or after a non-kernel
+// operation, the wait has no effect.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---- launches (k_update.cu) ----
 cudaError_t scan_setup();
 void launch_estar_write(const Dev& d, const EOps& ops);

@@ -39,6 +39,7 @@ namespace bcg {
 // scratch of the level passes is static shared memory).
 template <typename DT, bool STATIC, int T>
 __global__ void __launch_bounds__(T, 1) k_accum_smem(AccArgs<DT> a) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LevelSmem<T> ls;
     __shared__ int s_tail, s_nbig;
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(T, 1) k_accum_smem(AccArgs<DT> a) {
 
 __global__ void k_bc_partial(int n, const int32_t* rows, const int32_t* count, const ff* Dl,
                              ff* partial, const int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int total = rows ? *count : n;
@@ -66,6 +68,7 @@ __global__ void k_bc_partial(int n, const int32_t* rows, const int32_t* count, c
 constexpr int kBcUnroll = 8;
 __global__ void __launch_bounds__(256) k_bc_partial2(int n, const int32_t* rows, const int32_t* count,
                                                      const ff* Dl, ff* partial, const int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int total = rows ? *count : n;
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(256) k_bc_partial2(int n, const int32_t* rows,
 
 __global__ void k_bc_finish(int n, const int32_t* rows, const int32_t* count, const ff* partial,
                             double sign, int overwrite, double* hi, double* lo, const int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) dev_bc_finish(t, n, rows ? *count : n, partial, sign, overwrite, hi, lo);
@@ -168,8 +172,8 @@ template <typename DT, int T>
 static void accum_t(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
     const int grid = d.acc_grid;
     const size_t smem = (size_t)d.acc_smem;
-    if (is_static) k_accum_smem<DT, true, T><<<grid, T, smem, d.st>>>(acc_args<DT>(d, rows, count));
-    else k_accum_smem<DT, false, T><<<grid, T, smem, d.st>>>(acc_args<DT>(d, rows, count));
+    if (is_static) launch_k(k_accum_smem<DT, true, T>, grid, T, smem, d.st, acc_args<DT>(d, rows, count));
+    else launch_k(k_accum_smem<DT, false, T>, grid, T, smem, d.st, acc_args<DT>(d, rows, count));
 }
 
 static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
@@ -201,11 +205,11 @@ static void bc_rows(const Dev& d, int sign, int is_static, const int32_t* rows, 
     if (d.n % 2 == 0) {
         const int tb2 = (d.n / 2 + 255) / 256;
         dim3 g2(tb2, bc_row_ctas(d, tb2));
-        k_bc_partial2<<<g2, 256, 0, d.st>>>(d.n, rows, count, d.Dl, d.partial, d.err);
+        launch_k(k_bc_partial2, g2, 256, 0, d.st, d.n, rows, count, d.Dl, d.partial, d.err);
     } else {
-        k_bc_partial<<<g1, 256, 0, d.st>>>(d.n, rows, count, d.Dl, d.partial, d.err);
+        launch_k(k_bc_partial, g1, 256, 0, d.st, d.n, rows, count, d.Dl, d.partial, d.err);
     }
-    k_bc_finish<<<tb, 256, 0, d.st>>>(d.n, rows, count, d.partial, (double)sign, is_static, d.bc_hi, d.bc_lo,
+    launch_k(k_bc_finish, tb, 256, 0, d.st, d.n, rows, count, d.partial, (double)sign, is_static, d.bc_hi, d.bc_lo,
                                       d.err);
 }
 

@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pair_lists(int n, uint8_t* 
                                                                 int tcap, int32_t* acc_rows, int32_t* acc_count,
                                                                 int32_t* full_rows, int32_t* full_count,
                                                                 int64_t* stats, const int32_t* err) {
+    pdl_enter();
     constexpr int E = kCompactPerThread;
     static_assert(kCompactThreads * E < (1 << 16), "a tile's counts fit 16 bits");
     __shared__ int32_t wsum[32];
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pair_lists(int n, uint8_t* 
 // cleared whole.  The rows sent to the full path are added to stats[7].
 __global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t* tcnt, const int32_t* tlist,
                              int tcap, uint32_t* chg, int words, const int32_t* full_count, int64_t* stats) {
+    pdl_enter();
     const int cnt = *count;
     if (blockIdx.x == 0 && threadIdx.x == 0) stats[7] += *full_count;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -207,6 +209,7 @@ constexpr int kPlanThreads = 256;
 
 template <typename DT>
 __global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
+    pdl_enter();
     __shared__ int32_t s_val[kPlanThreads / 32][kPairCap];
     if (*a.err) return;
     const int n = a.n;
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
                                                        int32_t* prows, int32_t* pcount,
                                                        int64_t* wpre, int64_t* stats, int32_t* next_piece,
                                                        int32_t* walk_ctl, int32_t* walk_rowE, const int32_t* err) {
+    pdl_enter();
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_total;
     __shared__ int64_t s_rows[32], s_tgts[32];
@@ -618,6 +622,7 @@ __device__ __forceinline__ void pair_item(const PairArgs<DT>& a, int s, int U_, 
 // staged in shared memory when the CTA meets the row.
 template <typename DT, int VN>
 __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairArgs<DT> a) {
+    pdl_enter();
     __shared__ TgtFast<DT> s_fa[kPairCap];
     __shared__ TgtSlow s_sl[kPairCap];
     __shared__ ff s_acc[VN][kPairThreads];   // per thread: the sums of its VN columns
@@ -694,6 +699,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
 // so A' * 2^-24 and B' * 2^-56 are exact doubles, added with TwoSum as in
 // dev_bc_finish.
 __global__ void k_bc_fix(int n, int64_t* fix, double* hi, double* lo, const int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -728,12 +734,12 @@ PairRec pair_rec(const Dev& d) {
 }
 
 void launch_pair_lists(const Dev& d) {
-    k_pair_lists<<<1, kCompactThreads, 0, d.st>>>(d.n, d.changed, d.tcnt, d.tcap, d.acc_rows, d.counts + 1,
+    launch_k(k_pair_lists, 1, kCompactThreads, 0, d.st, d.n, d.changed, d.tcnt, d.tcap, d.acc_rows, d.counts + 1,
                                                   d.full_rows, d.counts + 3, d.stats, d.err);
 }
 
 void launch_pair_clear(const Dev& d) {
-    k_pair_clear<<<d.nsm * 4, 256, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tlist, d.tcap, d.chg,
+    launch_k(k_pair_clear, d.nsm * 4, 256, 0, d.st, d.acc_rows, d.counts + 1, d.tcnt, d.tlist, d.tcap, d.chg,
                                               d.chg_words, d.counts + 3, d.stats);
 }
 
@@ -832,6 +838,7 @@ __device__ __forceinline__ int64_t unit_start(const PairArgs<DT>& a, int nchunks
 
 template <typename DT>
 __global__ void __launch_bounds__(kWalkThreads, kWalkCtasPerSm) k_walk_units(PairArgs<DT> a, WalkArgs<DT> w) {
+    pdl_enter();
     extern __shared__ uint32_t wbits[];   // per warp: visited bits
     if (*a.err) return;
     const int n = a.n, words = a.words;
@@ -1008,6 +1015,7 @@ __device__ __forceinline__ ff fix_to_ff(long long A, long long B) {
 
 template <typename DT>
 __global__ void __launch_bounds__(kWalkThreads, kWalkRowCtasPerSm) k_walk_rows(PairArgs<DT> a, WalkArgs<DT> w) {
+    pdl_enter();
     extern __shared__ uint32_t tbits[];   // touched columns of the row
     __shared__ int s_r, s_nt;
     if (*a.err) return;
@@ -1101,6 +1109,7 @@ static_assert(WalkMid::smem <= 48 * 1024 && WalkLight::smem <= 48 * 1024, "no op
 
 template <typename DT, typename H>
 __global__ void __launch_bounds__(H::threads, H::ctas) k_walk_rows_hash(PairArgs<DT> a, WalkArgs<DT> w) {
+    pdl_enter();
     extern __shared__ unsigned long long hsm[];
     unsigned long long* hval = hsm;                                        // [2 * hash]
     int32_t* hkey = reinterpret_cast<int32_t*>(hsm + 2 * H::hash);         // [hash]
@@ -1201,36 +1210,34 @@ static void launch_walks(const Dev& d, const WalkUpd& upd, int nchunks, int vn) 
     const int grid = d.nsm * kWalkCtasPerSm, rgrid = d.nsm * kWalkRowCtasPerSm;
     WalkArgs<DT> w{d.e_off, d.e_len, (const Arc<DT>*)d.e_arc, d.walk_list, d.walk_buf, d.walk_cap, d.walk_useg,
                    d.walk_acc2, d.walk_tl, d.walk_ctl, d.walk_rowE, d.stats, nchunks, upd};
-    k_walk_units<DT><<<grid, kWalkThreads, walk_smem(d.n), d.st>>>(pair_args<DT>(d), w);
-    k_walk_rows<DT><<<rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), d.st>>>(pair_args<DT>(d), w);
-    k_walk_rows_hash<DT, WalkLight><<<d.nsm * WalkLight::ctas, WalkLight::threads, WalkLight::smem, d.st>>>(
-        pair_args<DT>(d), w);
-    k_walk_rows_hash<DT, WalkMid><<<d.nsm * WalkMid::ctas, WalkMid::threads, WalkMid::smem, d.st>>>(
-        pair_args<DT>(d), w);
+    launch_k(k_walk_units<DT>, grid, kWalkThreads, walk_smem(d.n), d.st, pair_args<DT>(d), w);
+    launch_k(k_walk_rows<DT>, rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), d.st, pair_args<DT>(d), w);
+    launch_k(k_walk_rows_hash<DT, WalkLight>, d.nsm * WalkLight::ctas, WalkLight::threads, WalkLight::smem, d.st, pair_args<DT>(d), w);
+    launch_k(k_walk_rows_hash<DT, WalkMid>, d.nsm * WalkMid::ctas, WalkMid::threads, WalkMid::smem, d.st, pair_args<DT>(d), w);
     // the column test, which does nothing unless the walks' buffer overflowed
     PairArgs<DT> a = pair_args<DT>(d);
     a.gate = d.walk_ctl + 4;
     const int pgrid = d.nsm * kPairCtasPerSm;
     if constexpr (sizeof(DT) == 4) {
-        if (vn == 8) k_pairdep<DT, 8><<<pgrid, kPairThreads, 0, d.st>>>(a);
-        else if (vn == 4) k_pairdep<DT, 4><<<pgrid, kPairThreads, 0, d.st>>>(a);
-        else k_pairdep<DT, 1><<<pgrid, kPairThreads, 0, d.st>>>(a);
+        if (vn == 8) launch_k(k_pairdep<DT, 8>, pgrid, kPairThreads, 0, d.st, a);
+        else if (vn == 4) launch_k(k_pairdep<DT, 4>, pgrid, kPairThreads, 0, d.st, a);
+        else launch_k(k_pairdep<DT, 1>, pgrid, kPairThreads, 0, d.st, a);
     } else {
-        if (vn == 2) k_pairdep<DT, 2><<<pgrid, kPairThreads, 0, d.st>>>(a);
-        else k_pairdep<DT, 1><<<pgrid, kPairThreads, 0, d.st>>>(a);
+        if (vn == 2) launch_k(k_pairdep<DT, 2>, pgrid, kPairThreads, 0, d.st, a);
+        else launch_k(k_pairdep<DT, 1>, pgrid, kPairThreads, 0, d.st, a);
     }
 }
 
 void launch_pairdep(const Dev& d, const WalkUpd* upd) {
     const int pgrid = d.nsm * 8;
-    if (d.dbytes == 4) k_pair_plan<int32_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int32_t>(d));
-    else k_pair_plan<int64_t><<<pgrid, kPlanThreads, 0, d.st>>>(pair_args<int64_t>(d));
+    if (d.dbytes == 4) launch_k(k_pair_plan<int32_t>, pgrid, kPlanThreads, 0, d.st, pair_args<int32_t>(d));
+    else launch_k(k_pair_plan<int64_t>, pgrid, kPlanThreads, 0, d.st, pair_args<int64_t>(d));
     // columns per thread: 16-byte (or two 16-byte) loads where n allows them
     const int vn = (d.dbytes == 4) ? ((kPairVec32 == 8 && d.n % 8 == 0) ? 8 : (d.n % 4 == 0 ? 4 : 1))
                                    : (d.n % 2 == 0 ? 2 : 1);
     const int cw = kPairThreads * vn;
     const int nchunks = (d.n + cw - 1) / cw;
-    k_pair_weights<<<1, 1024, 0, d.st>>>(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows,
+    launch_k(k_pair_weights, 1, 1024, 0, d.st, d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows,
                                           d.counts + 5, d.pair_w, d.stats, d.counts + 4, upd ? d.walk_ctl : nullptr,
                                           upd ? d.walk_rowE : nullptr, d.err);
     if (upd) {
@@ -1240,17 +1247,17 @@ void launch_pairdep(const Dev& d, const WalkUpd* upd) {
     }
     const int grid = d.nsm * kPairCtasPerSm;   // one resident wave; later pieces go to the first free CTA
     if (d.dbytes == 4) {
-        if (vn == 8) k_pairdep<int32_t, 8><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
-        else if (vn == 4) k_pairdep<int32_t, 4><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
-        else k_pairdep<int32_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int32_t>(d));
+        if (vn == 8) launch_k(k_pairdep<int32_t, 8>, grid, kPairThreads, 0, d.st, pair_args<int32_t>(d));
+        else if (vn == 4) launch_k(k_pairdep<int32_t, 4>, grid, kPairThreads, 0, d.st, pair_args<int32_t>(d));
+        else launch_k(k_pairdep<int32_t, 1>, grid, kPairThreads, 0, d.st, pair_args<int32_t>(d));
     } else {
-        if (vn == 2) k_pairdep<int64_t, 2><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
-        else k_pairdep<int64_t, 1><<<grid, kPairThreads, 0, d.st>>>(pair_args<int64_t>(d));
+        if (vn == 2) launch_k(k_pairdep<int64_t, 2>, grid, kPairThreads, 0, d.st, pair_args<int64_t>(d));
+        else launch_k(k_pairdep<int64_t, 1>, grid, kPairThreads, 0, d.st, pair_args<int64_t>(d));
     }
 }
 
 void launch_bc_fix(const Dev& d) {
-    k_bc_fix<<<(d.n + 255) / 256, 256, 0, d.st>>>(d.n, d.bcfix, d.bc_hi, d.bc_lo, d.err);
+    launch_k(k_bc_fix, (d.n + 255) / 256, 256, 0, d.st, d.n, d.bcfix, d.bc_hi, d.bc_lo, d.err);
 }
 
 }  // namespace bcg

@@ -24,6 +24,7 @@
 namespace bcg {
 
 __global__ void k_estar_write(int32_t* e_src, void* e_arc, int32_t* e_len, int dbytes, EOps ops) {
+    pdl_enter();
     int i = threadIdx.x;
     if (i >= ops.count) return;
     const EOp o = ops.op[i];
@@ -39,6 +40,7 @@ __global__ void k_estar_write(int32_t* e_src, void* e_arc, int32_t* e_len, int d
 // Source and destination ranges of all moves are disjoint.
 template <typename DT>
 __global__ void k_estar_move(int32_t* e_off, int32_t* e_src, Arc<DT>* e_arc, EMoves moves) {
+    pdl_enter();
     if ((int)blockIdx.x >= moves.count) return;
     const EMove m = moves.mv[blockIdx.x];
     for (int i = threadIdx.x; i < m.len; i += blockDim.x) {
@@ -54,6 +56,7 @@ __global__ void k_alg4_in(int n, const DT* __restrict__ D, const uint64_t* __res
                           int v, const VEdge* __restrict__ e, int k, int directed,
                           DT* fD, uint64_t* fS, uint64_t* fM, uint8_t* mark, uint8_t* changed,
                           int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -66,6 +69,7 @@ __global__ void k_rows_out(int n, const DT* __restrict__ D, const uint64_t* __re
                            int v, const VEdge* __restrict__ e, int k, int directed,
                            DT* fD, uint64_t* fS, uint64_t* fM, uint8_t* mark, uint8_t* changed,
                            int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) dev_rows_out<DT>(s, n, D, S, v, e, k, directed, fD, fS, fM, mark, changed, err);
@@ -75,6 +79,7 @@ template <typename DT>
 __global__ void k_alg4_out(int n, const DT* __restrict__ D, const uint64_t* __restrict__ S,
                            int v, const VEdge* __restrict__ e, int k, int directed,
                            DT* cD, uint64_t* cS, uint64_t* cM, uint8_t* changed, int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) dev_alg4_out<DT>(t, n, D, S, v, e, k, directed, cD, cS, cM, changed, err);
@@ -83,6 +88,7 @@ __global__ void k_alg4_out(int n, const DT* __restrict__ D, const uint64_t* __re
 __global__ void __launch_bounds__(kCompactThreads)
 k_compact(int n, uint8_t* mark, int clear, int32_t* rows, int32_t* count, int full,
           int64_t* stats, const int32_t* err) {
+    pdl_enter();
     dev_compact(n, mark, clear, rows, count, full, stats, err);
 }
 
@@ -93,6 +99,7 @@ k_compact(int n, uint8_t* mark, int clear, int32_t* rows, int32_t* count, int fu
 // is read only on ties and written only where the pair changes.
 template <typename DT, bool VECTOR>
 __global__ void __launch_bounds__(kScanThreads, 4) k_scan(ScanArgs<DT> a) {
+    pdl_enter();
     // warp-uniform early exit: the warp sum at the end needs every lane
     int bad = 0;
     if ((threadIdx.x & 31) == 0) bad = *reinterpret_cast<volatile int32_t*>(a.err);
@@ -155,6 +162,7 @@ __device__ __forceinline__ void cs_wait_all() { asm volatile("cp.async.wait_all;
 // DUAL: two row lists, each with its own column vector (a.rows2 set).
 template <typename DT, bool WHOLE, bool DUAL>
 __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<DT> a, int nch) {
+    pdl_enter();
     using V = Vec<DT>;
     using VT = typename V::T;
     constexpr int VN = V::N;
@@ -368,6 +376,7 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
 template <typename DT>
 __global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, const uint64_t* cS, PairRec rec,
                             const int32_t* err) {
+    pdl_enter();
     if (*err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -383,6 +392,7 @@ __global__ void k_write_row(int n, DT* D, uint64_t* S, int v, const DT* cD, cons
 template <typename DT>
 __global__ void k_estar_keep(int n, const DT* D, const int32_t* e_src, const Arc<DT>* e_arc,
                              int64_t cap, uint8_t* keep) {
+    pdl_enter();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= cap) return;
     const Arc<DT> a = e_arc[e];
@@ -408,6 +418,7 @@ __global__ void k_edge_prep(int n, const DT* D, const uint64_t* S, int u, int v,
                             uint64_t* cSv, DT* cDu, uint64_t* cSu, DT* fD, uint64_t* fS, uint64_t* fM,
                             int32_t* rows1, int32_t* count1, int32_t* rows2, int32_t* count2,
                             uint8_t* changed, int32_t* err) {
+    pdl_enter();
     if (*reinterpret_cast<const volatile int32_t*>(err)) return;   // grid-uniform for this launch
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -468,53 +479,47 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_estar_write(const Dev& d, const EOps& ops) {
     if (ops.count <= 0) return;
-    k_estar_write<<<1, kMaxEOps, 0, d.st>>>(d.e_src, d.e_arc, d.e_len, d.dbytes, ops);
+    launch_k(k_estar_write, 1, kMaxEOps, 0, d.st, d.e_src, d.e_arc, d.e_len, d.dbytes, ops);
 }
 
 void launch_estar_move(const Dev& d, const EMoves& moves) {
     if (moves.count <= 0) return;
     if (d.dbytes == 4)
-        k_estar_move<int32_t><<<moves.count, 128, 0, d.st>>>(d.e_off, d.e_src, (Arc<int32_t>*)d.e_arc, moves);
+        launch_k(k_estar_move<int32_t>, moves.count, 128, 0, d.st, d.e_off, d.e_src, (Arc<int32_t>*)d.e_arc, moves);
     else
-        k_estar_move<int64_t><<<moves.count, 128, 0, d.st>>>(d.e_off, d.e_src, (Arc<int64_t>*)d.e_arc, moves);
+        launch_k(k_estar_move<int64_t>, moves.count, 128, 0, d.st, d.e_off, d.e_src, (Arc<int64_t>*)d.e_arc, moves);
 }
 
 void launch_alg4_in(const Dev& d, int32_t v, const VEdge* e, int32_t k) {
     if (d.dbytes == 4)
-        k_alg4_in<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.S, v, e, k, d.directed, (int32_t*)d.fD, d.fS, d.fM,
+        launch_k(k_alg4_in<int32_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (const int32_t*)d.D, d.S, v, e, k, d.directed, (int32_t*)d.fD, d.fS, d.fM,
             d.mark, d.changed, d.err);
     else
-        k_alg4_in<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.S, v, e, k, d.directed, (int64_t*)d.fD, d.fS, d.fM,
+        launch_k(k_alg4_in<int64_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (const int64_t*)d.D, d.S, v, e, k, d.directed, (int64_t*)d.fD, d.fS, d.fM,
             d.mark, d.changed, d.err);
 }
 
 void launch_rows_out(const Dev& d, int32_t v, const VEdge* e, int32_t k) {
     if (d.dbytes == 4)
-        k_rows_out<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.S, v, e, k, d.directed, (int32_t*)d.fD, d.fS, d.fM,
+        launch_k(k_rows_out<int32_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (const int32_t*)d.D, d.S, v, e, k, d.directed, (int32_t*)d.fD, d.fS, d.fM,
             d.mark, d.changed, d.err);
     else
-        k_rows_out<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.S, v, e, k, d.directed, (int64_t*)d.fD, d.fS, d.fM,
+        launch_k(k_rows_out<int64_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (const int64_t*)d.D, d.S, v, e, k, d.directed, (int64_t*)d.fD, d.fS, d.fM,
             d.mark, d.changed, d.err);
 }
 
 void launch_alg4_out(const Dev& d, int32_t v, const VEdge* e, int32_t k) {
     if (d.dbytes == 4)
-        k_alg4_out<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.S, v, e, k, d.directed, (int32_t*)d.cD, d.cS, d.cM,
+        launch_k(k_alg4_out<int32_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (const int32_t*)d.D, d.S, v, e, k, d.directed, (int32_t*)d.cD, d.cS, d.cM,
             d.changed, d.err);
     else
-        k_alg4_out<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.S, v, e, k, d.directed, (int64_t*)d.cD, d.cS, d.cM,
+        launch_k(k_alg4_out<int64_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (const int64_t*)d.D, d.S, v, e, k, d.directed, (int64_t*)d.cD, d.cS, d.cM,
             d.changed, d.err);
 }
 
 void launch_compact(const Dev& d, const uint8_t* mark, int clear, int32_t* rows, int32_t* count,
                     int full, int stats) {
-    k_compact<<<1, kCompactThreads, 0, d.st>>>(d.n, const_cast<uint8_t*>(mark), clear, rows, count,
+    launch_k(k_compact, 1, kCompactThreads, 0, d.st, d.n, const_cast<uint8_t*>(mark), clear, rows, count,
                                                full, stats ? d.stats : nullptr, d.err);
 }
 
@@ -545,14 +550,14 @@ static void scan_dispatch(const Dev& d, ScanArgs<DT> a) {
         const int per = std::max(1, d.nsm * kCsCtasPerSm / nch);
         const bool whole = d.n % CW == 0;
         if (a.rows2) {
-            if (whole) k_scan_cs<DT, true, true><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
-            else k_scan_cs<DT, false, true><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+            if (whole) launch_k(k_scan_cs<DT, true, true>, nch * per, kCsThreads, kCsSmem, d.st, a, nch);
+            else launch_k(k_scan_cs<DT, false, true>, nch * per, kCsThreads, kCsSmem, d.st, a, nch);
         } else {
-            if (whole) k_scan_cs<DT, true, false><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
-            else k_scan_cs<DT, false, false><<<nch * per, kCsThreads, kCsSmem, d.st>>>(a, nch);
+            if (whole) launch_k(k_scan_cs<DT, true, false>, nch * per, kCsThreads, kCsSmem, d.st, a, nch);
+            else launch_k(k_scan_cs<DT, false, false>, nch * per, kCsThreads, kCsSmem, d.st, a, nch);
         }
     } else {
-        k_scan<DT, false><<<d.nsm * 8, kScanThreads, 0, d.st>>>(a);
+        launch_k(k_scan<DT, false>, d.nsm * 8, kScanThreads, 0, d.st, a);
     }
 }
 
@@ -630,10 +635,10 @@ void launch_write_row(const Dev& d, int32_t v) {
     PairRec rec = d.pair_on ? pair_rec(d) : PairRec{};
     rec.first = 1;
     if (d.dbytes == 4)
-        k_write_row<int32_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int32_t*)d.D, d.S, v,
+        launch_k(k_write_row<int32_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (int32_t*)d.D, d.S, v,
                                                                 (const int32_t*)d.cD, d.cS, rec, d.err);
     else
-        k_write_row<int64_t><<<nblk(d.n, 256), 256, 0, d.st>>>(d.n, (int64_t*)d.D, d.S, v,
+        launch_k(k_write_row<int64_t>, nblk(d.n, 256), 256, 0, d.st, d.n, (int64_t*)d.D, d.S, v,
                                                                 (const int64_t*)d.cD, d.cS, rec, d.err);
 }
 
@@ -646,12 +651,10 @@ void launch_edge_prep(const Dev& d, int32_t u, int32_t v, int64_t w) {
     cudaMemsetAsync(d.counts, 0, 3 * sizeof(int32_t), d.st);   // counts[0..2]; [1] is rewritten later
     const int grid = (d.n + 255) / 256;
     if (d.dbytes == 4)
-        k_edge_prep<int32_t><<<grid, 256, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.S, u, v, w, (int32_t*)d.cD, d.cS, (int32_t*)d.cD2, d.cS2, (int32_t*)d.fD,
+        launch_k(k_edge_prep<int32_t>, grid, 256, 0, d.st, d.n, (const int32_t*)d.D, d.S, u, v, w, (int32_t*)d.cD, d.cS, (int32_t*)d.cD2, d.cS2, (int32_t*)d.fD,
             d.fS, d.fM, d.rows, d.counts, d.acc_rows, d.counts + 2, d.changed, d.err);
     else
-        k_edge_prep<int64_t><<<grid, 256, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.S, u, v, w, (int64_t*)d.cD, d.cS, (int64_t*)d.cD2, d.cS2, (int64_t*)d.fD,
+        launch_k(k_edge_prep<int64_t>, grid, 256, 0, d.st, d.n, (const int64_t*)d.D, d.S, u, v, w, (int64_t*)d.cD, d.cS, (int64_t*)d.cD2, d.cS2, (int64_t*)d.fD,
             d.fS, d.fM, d.rows, d.counts, d.acc_rows, d.counts + 2, d.changed, d.err);
 }
 
@@ -679,11 +682,9 @@ void launch_edge_scan(const Dev& d) {
 void launch_estar_keep(const Dev& d, uint8_t* keep) {
     if (d.e_cap <= 0) return;
     if (d.dbytes == 4)
-        k_estar_keep<int32_t><<<nblk(d.e_cap, 256), 256, 0, d.st>>>(
-            d.n, (const int32_t*)d.D, d.e_src, (const Arc<int32_t>*)d.e_arc, d.e_cap, keep);
+        launch_k(k_estar_keep<int32_t>, nblk(d.e_cap, 256), 256, 0, d.st, d.n, (const int32_t*)d.D, d.e_src, (const Arc<int32_t>*)d.e_arc, d.e_cap, keep);
     else
-        k_estar_keep<int64_t><<<nblk(d.e_cap, 256), 256, 0, d.st>>>(
-            d.n, (const int64_t*)d.D, d.e_src, (const Arc<int64_t>*)d.e_arc, d.e_cap, keep);
+        launch_k(k_estar_keep<int64_t>, nblk(d.e_cap, 256), 256, 0, d.st, d.n, (const int64_t*)d.D, d.e_src, (const Arc<int64_t>*)d.e_arc, d.e_cap, keep);
 }
 
 }  // namespace bcg
