@@ -148,6 +148,7 @@ constexpr int kCsVpt = 4;
 constexpr int kCsStages = 4;
 constexpr int kCsCtasPerSm = 3;
 constexpr size_t kCsRingBytes = (size_t)kCsStages * kCsVpt * kCsThreads * 16;
+constexpr int kCsQueue = 32 + 32 * kCsVpt;   // a warp's candidate queue: < 32 left over plus one row
 
 __device__ __forceinline__ void cs_copy16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
     // Candidate vectors (s, t) of this warp, waiting for the rule: applying it takes a
     // few dependent memory round trips, which the 32 lanes then take together instead
     // of one candidate at a time while the warp's row stream waits.
-    int2* wq = reinterpret_cast<int2*>(cs_smem + kCsRingBytes) + (tid >> 5) * 64;
+    int2* wq = reinterpret_cast<int2*>(cs_smem + kCsRingBytes) + (tid >> 5) * kCsQueue;
     int qn = 0;   // warp-uniform
     auto run_queued = [&](int count) {
         int s = -1, t = 0;
@@ -340,25 +341,27 @@ __global__ void __launch_bounds__(kCsThreads, kCsCtasPerSm) k_scan_cs(ScanArgs<D
                         if ((WHOLE || t < n) && quick_vec<DT>(stage[st][u][tid], cq[u], rq, false)) cand |= 1u << u;
                     }
                 }
-                // candidates go to the warp's queue; the rule runs 32 at a time
+                // candidates go to the warp's queue (a row adds at most 32 x kCsVpt); the
+                // rule runs 32 at a time, in one loop per row (inlined once per ring stage:
+                // a flush inside the vector loop put 16 copies of the rule into the kernel,
+                // too much code for the instruction cache on hub updates)
                 if (__any_sync(0xffffffffu, cand != 0u)) {
 #pragma unroll
                     for (int u = 0; u < kCsVpt; ++u) {
                         const bool mine = (cand >> u) & 1u;
                         const unsigned b = __ballot_sync(0xffffffffu, mine);
-                        if (!b) continue;
                         if (mine)
                             wq[qn + __popc(b & ((1u << lane) - 1u))] =
                                 make_int2(s, t0 + (u * kCsThreads + tid) * VN);
                         qn += __popc(b);
-                        if (qn >= 32) {
-                            __syncwarp();
-                            run_queued(32);
-                            __syncwarp();
-                            if (lane < qn - 32) wq[lane] = wq[32 + lane];
-                            qn -= 32;
-                            __syncwarp();
-                        }
+                    }
+                    while (qn >= 32) {
+                        __syncwarp();
+                        run_queued(32);
+                        __syncwarp();
+                        for (int i = lane; i < qn - 32; i += 32) wq[i] = wq[32 + i];
+                        qn -= 32;
+                        __syncwarp();
                     }
                 }
             }
@@ -524,8 +527,8 @@ void launch_compact(const Dev& d, const uint8_t* mark, int clear, int32_t* rows,
 }
 
 // Dynamic shared memory of k_scan_cs: its ring of kCsStages row chunks, then a queue
-// of 64 candidate vectors per warp.
-constexpr size_t kCsSmem = kCsRingBytes + (size_t)(kCsThreads / 32) * 64 * sizeof(int2);
+// of kCsQueue candidate vectors per warp.
+constexpr size_t kCsSmem = kCsRingBytes + (size_t)(kCsThreads / 32) * kCsQueue * sizeof(int2);
 
 // Allows the vector-path kernels their shared memory on the current device.
 cudaError_t scan_setup() {
