@@ -185,7 +185,8 @@ struct Dev {
     int32_t acc_grid;    // CTAs of the accumulation kernel
     int32_t acc_smem;    // dynamic shared memory of the accumulation kernel
     int32_t acc_mask_smem;  // 1: the DAG slot mask lives in shared memory
-    int32_t acc_threads;    // threads of an accumulation CTA (kAccThreadsWide or kAccThreadsNarrow)
+    int32_t acc_threads;    // kAccThreadsWide: wide CTAs allowed for partial waves of sources
+    int32_t acc_grid_wide;  // CTAs of the wide accumulation kernel (acc_grid: of the narrow one)
     int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
     int64_t ws_stride;
     // pair-dependency corrections (undirected graphs): the pairs changed by this update,
@@ -217,9 +218,10 @@ struct Dev {
 };
 
 constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction
-// Threads of an accumulation CTA (one source at a time): 1024 for graphs of at least
-// kAccWideMinN vertices (the level passes of one source spread over more threads), 512
-// otherwise (more sources in flight per SM); the batched path uses 512.
+// Threads of an accumulation CTA (one source at a time): 1024 for the few rows over the
+// target cap of an update on graphs of at least kAccWideMinN vertices (the level passes
+// of one source spread over more threads), 512 otherwise (two sources in flight per SM);
+// the batched path uses 512.
 constexpr int kAccThreadsWide = 1024;
 constexpr int kAccThreadsNarrow = 512;
 constexpr int kAccWideMinN = 4096;

@@ -152,16 +152,17 @@ void accum_config(Dev& d) {
     const size_t mb = mask_bytes(d.e_cap);
     const bool in_smem = base + mb <= kSmemLimit;
     const size_t smem = in_smem ? base + mb : base;
-    d.acc_threads = d.n >= kAccWideMinN ? kAccThreadsWide : kAccThreadsNarrow;
-    const bool wide = d.acc_threads == kAccThreadsWide;
-    int per_sm = d.dbytes == 4 ? (wide ? accum_occupancy<int32_t, kAccThreadsWide>(smem)
-                                       : accum_occupancy<int32_t, kAccThreadsNarrow>(smem))
-                               : (wide ? accum_occupancy<int64_t, kAccThreadsWide>(smem)
-                                       : accum_occupancy<int64_t, kAccThreadsNarrow>(smem));
+    int per_sm = d.dbytes == 4 ? accum_occupancy<int32_t, kAccThreadsNarrow>(smem)
+                               : accum_occupancy<int64_t, kAccThreadsNarrow>(smem);
+    int per_sm_w = d.dbytes == 4 ? accum_occupancy<int32_t, kAccThreadsWide>(smem)
+                                 : accum_occupancy<int64_t, kAccThreadsWide>(smem);
     if (per_sm < 1) per_sm = 1;
+    if (per_sm_w < 1) per_sm_w = 1;
+    d.acc_threads = d.n >= kAccWideMinN ? kAccThreadsWide : kAccThreadsNarrow;
     d.acc_smem = (int32_t)smem;
     d.acc_mask_smem = in_smem ? 1 : 0;
-    d.acc_grid = std::min(d.nsm * per_sm, std::max(d.n, 1));
+    d.acc_grid = std::min(d.nsm * std::max(per_sm, per_sm_w), std::max(d.n, 1));
+    d.acc_grid_wide = std::min(d.nsm * per_sm_w, d.acc_grid);
     // per CTA: rho (n float-float pairs) | level bounds (n + 2 ints) | slot mask if not in smem
     const int64_t head = ((3 * (int64_t)d.n + 2) + 3) & ~(int64_t)3;
     d.ws_stride = head + (in_smem ? 0 : (((int64_t)mb / 4 + 3) & ~(int64_t)3));
@@ -170,14 +171,19 @@ void accum_config(Dev& d) {
 // Algorithm 1 for the sources listed in rows[0..*count), or for every source.
 template <typename DT, int T>
 static void accum_t(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
-    const int grid = d.acc_grid;
+    const int grid = T == kAccThreadsWide ? d.acc_grid_wide : d.acc_grid;
     const size_t smem = (size_t)d.acc_smem;
     if (is_static) launch_k(k_accum_smem<DT, true, T>, grid, T, smem, d.st, acc_args<DT>(d, rows, count));
     else launch_k(k_accum_smem<DT, false, T>, grid, T, smem, d.st, acc_args<DT>(d, rows, count));
 }
 
+// The wide CTAs serve a partial wave of sources (the rows over the target cap of an
+// update with pair corrections: tens per update), where one source's latency is the
+// time, and the static computation (measured at n = 16384: 139 ms wide, 148 ms narrow);
+// every changed row of an update without pair corrections (thousands of sources) is
+// served faster by the narrow ones, two per SM (n = 8192: 4.1 ms against 5.6 ms).
 static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
-    const bool wide = d.acc_threads == kAccThreadsWide;
+    const bool wide = d.acc_threads == kAccThreadsWide && (is_static || d.pair_on);
     if (d.dbytes == 4) {
         if (wide) accum_t<int32_t, kAccThreadsWide>(d, is_static, rows, count);
         else accum_t<int32_t, kAccThreadsNarrow>(d, is_static, rows, count);
