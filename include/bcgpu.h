@@ -255,6 +255,16 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
  *                     for s.  Off: every changed source is re-accumulated (Section 5).
  *                     The two give the same D and sigma bit for bit and dependencies
  *                     within rounding.
+ *   "fused_edges" 0|1 (on by default): an undirected edge update runs one rank-1 pass
+ *                     over both directions of the edge, each row's candidate taken from
+ *                     the state before the update (Section 3 "Undirected graphs" as one
+ *                     pass); 0: the two directed passes one after the other.  Same
+ *                     results bit for bit.
+ *   "wide_accum" 0|1 (on by default): on graphs of at least 4096 vertices, re-run
+ *                     Algorithm 1 for the rows over the target cap in 1024-thread CTAs
+ *                     (one source's passes spread over more threads); 0: 512-thread
+ *                     CTAs, which share SMs better with other handles' work (the server
+ *                     sets 0 for its graphs).  Same results bit for bit.
  *   "pair_walk" 0|1 (undirected graphs only; BC_ERR_ARG on a directed graph): find the
  *                     columns of each changed pair (s,t) -- the vertices on a shortest
  *                     s-t path of the old and of the new state -- by walking DAG(s) of

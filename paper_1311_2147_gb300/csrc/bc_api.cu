@@ -773,27 +773,23 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
             return off[a + 1] - off[a] > off[b + 1] - off[b];
         });
-        if ((rc = dalloc(g, &d.p_dst, arcs)) || (rc = dalloc(g, &d.s_order, n)))
-            return bail(rc, "device allocation failed");
+        // scratch in the dependency rows (n^2 float-float pairs, >= 4 (arcs + n) bytes),
+        // which the accumulation writes only after the searches: no allocation here (a
+        // cudaFree waits for the whole device, other handles' work included)
+        d.p_dst = reinterpret_cast<int32_t*>(d.Dl);
+        d.s_order = d.p_dst + arcs;
         CKI(cudaMemcpyAsync(d.p_dst, d.g_dst, sizeof(int32_t) * arcs, cudaMemcpyDeviceToDevice, d.st));
         CKI(cudaMemcpyAsync(d.s_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, d.st));
     }
     launch_sssp(d);
-    uint8_t* d_flags = nullptr;
-    if ((rc = dalloc(g, &d_flags, arcs))) return bail(rc, "device allocation failed");
+    // the E* flags, also in the dependency rows' memory (free until the accumulation)
+    uint8_t* d_flags = reinterpret_cast<uint8_t*>(d.Dl);
     launch_estar_flags(d, d_flags);
     std::vector<uint8_t> eflags(arcs);
     CKI(cudaMemcpyAsync(eflags.data(), d_flags, arcs, cudaMemcpyDeviceToHost, d.st));
     CKI(cudaStreamSynchronize(d.st));
     CKI(cudaGetLastError());
-    dfree(g, d_flags);
-    g->bytes -= (int64_t)std::max<int64_t>(arcs, 1);
-    if (prune) {
-        dfree(g, d.p_dst);
-        dfree(g, d.s_order);
-        g->bytes -= 4 * (int64_t)std::max<int64_t>(arcs, 1) + 4 * (int64_t)n;
-        d.p_dst = d.s_order = nullptr;
-    }
+    d.p_dst = d.s_order = nullptr;
     {
         std::vector<HArc> estar;
         for (int64_t i = 0; i < arcs; ++i)
@@ -1137,6 +1133,14 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
     if (!g || !name) return BC_ERR_ARG;
     if (std::strcmp(name, "full_scan") == 0) {
         g->full_scan = value != 0;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "wide_accum") == 0) {
+        // 1024-thread accumulation CTAs for the rows over the target cap (graphs of at
+        // least 4096 vertices); 0: 512-thread ones, which share SMs better with the work of
+        // other handles running at the same time (the server turns them off)
+        g->d.acc_narrow_only = value != 0 ? 0 : 1;
+        g->d.acc_threads = (value != 0 && g->n >= kAccWideMinN) ? kAccThreadsWide : kAccThreadsNarrow;
         return BC_OK;
     }
     if (std::strcmp(name, "fused_edges") == 0) {

@@ -186,6 +186,7 @@ struct Dev {
     int32_t acc_smem;    // dynamic shared memory of the accumulation kernel
     int32_t acc_mask_smem;  // 1: the DAG slot mask lives in shared memory
     int32_t acc_threads;    // kAccThreadsWide: wide CTAs allowed for partial waves of sources
+    int32_t acc_narrow_only;  // 1: never the wide CTAs (kept across launch-shape updates)
     int32_t acc_grid_wide;  // CTAs of the wide accumulation kernel (acc_grid: of the narrow one)
     int32_t* ws;         // accumulation work space, acc_grid * ws_stride ints
     int64_t ws_stride;

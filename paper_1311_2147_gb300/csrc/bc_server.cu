@@ -121,6 +121,8 @@ int admit(bc_server* s, int32_t gid) {
         r.h = nullptr;
         return rc;
     }
+    // resident graphs run side by side: narrow accumulation CTAs leave room on each SM
+    bc_set_option(r.h, "wide_accum", 0);
     s->used += r.bytes;
     s->admissions++;
     return BC_OK;

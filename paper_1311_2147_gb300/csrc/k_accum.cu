@@ -38,7 +38,7 @@ namespace bcg {
 // One CTA per source at a time (shared memory as described at AccSmem; the per-round
 // scratch of the level passes is static shared memory).
 template <typename DT, bool STATIC, int T>
-__global__ void __launch_bounds__(T, 1) k_accum_smem(AccArgs<DT> a) {
+__global__ void __launch_bounds__(T, 1024 / T) k_accum_smem(AccArgs<DT> a) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LevelSmem<T> ls;
@@ -158,7 +158,7 @@ void accum_config(Dev& d) {
                                  : accum_occupancy<int64_t, kAccThreadsWide>(smem);
     if (per_sm < 1) per_sm = 1;
     if (per_sm_w < 1) per_sm_w = 1;
-    d.acc_threads = d.n >= kAccWideMinN ? kAccThreadsWide : kAccThreadsNarrow;
+    d.acc_threads = (d.n >= kAccWideMinN && !d.acc_narrow_only) ? kAccThreadsWide : kAccThreadsNarrow;
     d.acc_smem = (int32_t)smem;
     d.acc_mask_smem = in_smem ? 1 : 0;
     d.acc_grid = std::min(d.nsm * std::max(per_sm, per_sm_w), std::max(d.n, 1));
