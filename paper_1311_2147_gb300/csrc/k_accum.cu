@@ -179,11 +179,14 @@ static void accum_t(const Dev& d, int is_static, const int32_t* rows, const int3
 
 // The wide CTAs serve a partial wave of sources (the rows over the target cap of an
 // update with pair corrections: tens per update), where one source's latency is the
-// time, and the static computation (measured at n = 16384: 139 ms wide, 148 ms narrow);
-// every changed row of an update without pair corrections (thousands of sources) is
-// served faster by the narrow ones, two per SM (n = 8192: 4.1 ms against 5.6 ms).
+// time (BA n = 16384: 0.30 ms per update wide, 0.41 ms narrow), and the static
+// computation on the largest graphs (n = 16384: 139 ms wide, 141 ms narrow; n = 8192:
+// 33.7 ms wide, 30.5 ms narrow).  Every changed row of an update without pair
+// corrections (thousands of sources) is served faster by the narrow ones, two per SM.
+constexpr int kAccStaticWideMinN = 16384;
+
 static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {
-    const bool wide = d.acc_threads == kAccThreadsWide && (is_static || d.pair_on);
+    const bool wide = d.acc_threads == kAccThreadsWide && (is_static ? d.n >= kAccStaticWideMinN : d.pair_on != 0);
     if (d.dbytes == 4) {
         if (wide) accum_t<int32_t, kAccThreadsWide>(d, is_static, rows, count);
         else accum_t<int32_t, kAccThreadsNarrow>(d, is_static, rows, count);

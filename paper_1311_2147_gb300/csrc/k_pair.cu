@@ -815,18 +815,24 @@ constexpr int kWalkGrab = 1;         // units a warp takes at a time (unit costs
 constexpr int kWalkLightRowMax = 128;   // rows whose walks found at most this many vertices: light CTAs
 constexpr int kWalkMidRowMax = 512;     // up to this many: mid-size CTAs; more: k_walk_rows
 
-// d(s,x) of a state: the saved value where the pair changed in this update (old state).
+// d(s,x) and sigma_sx of a state: the saved values where the pair changed in this update
+// (old state).  The change-map word and the current value are loaded together (one
+// round trip); the saved value is read only where the bit is set, rarely.
 template <typename DT>
 __device__ __forceinline__ int64_t walk_d(const PairArgs<DT>& a, size_t rs, int s, int x, bool is_new) {
     const size_t i = rs + x;
-    if (!is_new && ((a.chg[(size_t)s * a.words + (x >> 5)] >> (x & 31)) & 1u)) return (int64_t)a.oD[i];
-    return (int64_t)a.D[i];
+    const int64_t cur = (int64_t)a.D[i];
+    if (is_new) return cur;
+    const uint32_t word = a.chg[(size_t)s * a.words + (x >> 5)];
+    return ((word >> (x & 31)) & 1u) ? (int64_t)a.oD[i] : cur;
 }
 template <typename DT>
 __device__ __forceinline__ uint64_t walk_sigma(const PairArgs<DT>& a, size_t rs, int s, int x, bool is_new) {
     const size_t i = rs + x;
-    if (!is_new && ((a.chg[(size_t)s * a.words + (x >> 5)] >> (x & 31)) & 1u)) return a.oS[i];
-    return a.S[i];
+    const uint64_t cur = a.S[i];
+    if (is_new) return cur;
+    const uint32_t word = a.chg[(size_t)s * a.words + (x >> 5)];
+    return ((word >> (x & 31)) & 1u) ? a.oS[i] : cur;
 }
 
 // First unit of row index r: the targets of the rows before it (wpre counts T + 1 per
