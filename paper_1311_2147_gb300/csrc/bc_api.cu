@@ -1220,6 +1220,7 @@ struct bc_batch {
     int64_t* d_voff = nullptr;
     int64_t* d_coff = nullptr;
     int64_t* d_plans = nullptr;
+    int32_t* d_pctr = nullptr;
     int32_t* d_ws = nullptr;
     int64_t R_cap = 0, E_cap = 0, O_cap = 0, ws_cap = 0;
     cudaGraphExec_t exec = nullptr;
@@ -1321,7 +1322,8 @@ int bc_batch_create(bc_batch** out, int32_t count, bc_graph* const* graphs, void
     b->L.scan_sched = 0;
     int rc;
     if ((rc = balloc(b, &b->d_devs, count)) || (rc = balloc(b, &b->d_coff, count + 1)) ||
-        (rc = balloc(b, &b->d_plans, 3 * ((size_t)count + 1)))) {
+        (rc = balloc(b, &b->d_plans, (4 + (size_t)kPairClasses) * ((size_t)count + 1))) ||
+        (rc = balloc(b, &b->d_pctr, kPairClasses))) {
         bc_batch_destroy(b);
         return rc;
     }
@@ -1466,6 +1468,15 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
         }
     }
     // ---- device buffers and launch shape
+    // graphs with pair corrections (undirected, option on) by class of the column test's
+    // columns per thread: the set of pair kernels a round launches
+    int32_t pair_classes = 0;
+    for (bc_graph* g : b->graphs)
+        if (g->d.pair_on) pair_classes |= 1 << pair_class(g->dbytes, pair_vn(g->dbytes, g->n));
+    if (pair_classes != b->L.pair_classes) {
+        b->L.pair_classes = pair_classes;
+        drop_exec(b);
+    }
     int64_t cap_max = 0;
     for (bc_graph* g : b->graphs) cap_max = std::max(cap_max, g->d.e_cap);
     if (cap_max != b->cap_max) {
@@ -1533,6 +1544,9 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
     a.plan_scan = b->d_plans;
     a.plan_bc = b->d_plans + (G + 1);
     a.plan_acc = b->d_plans + 2 * (G + 1);
+    a.plan_pr = b->d_plans + 3 * (G + 1);
+    a.plan_pw = b->d_plans + 4 * (G + 1);
+    a.pctr = b->d_pctr;
     a.ws = b->d_ws;
     a.ws_stride = b->L.ws_stride;
     b->L.max_eops = std::max<int64_t>(b->L.max_eops, 256);

@@ -243,6 +243,28 @@ struct PairRec {
     int32_t first;       // no pair has changed yet in this update (the IN phase; row v)
 };
 
+// The recording buffers of a handle with pair corrections.
+__host__ __device__ inline PairRec make_pair_rec(const Dev& d) {
+    PairRec r;
+    r.chg = d.chg;
+    r.chg_words = d.chg_words;
+    r.oldD = d.oldD;
+    r.oldS = d.oldS;
+    r.tcnt = d.tcnt;
+    r.tlist = d.tlist;
+    r.tcap = d.tcap;
+    r.first = 0;
+    return r;
+}
+
+// Columns per thread of the pair-correction column test for n vertices: 16-byte (or two
+// 16-byte) loads where every row starts on a 16-byte boundary.
+constexpr int kPairVec32 = 8;   // columns per thread with int32 distances (4 or 8)
+__host__ __device__ inline int pair_vn(int dbytes, int n) {
+    if (dbytes == 4) return (kPairVec32 == 8 && n % 8 == 0) ? 8 : (n % 4 == 0 ? 4 : 1);
+    return n % 2 == 0 ? 2 : 1;
+}
+
 // The first change of pair (s,t) in an update sets its bit, saves its old distance and
 // path count, and lists t as a changed target of row s (targets beyond the capacity
 // are only counted).  Later changes of the same pair (the OUT phase after the IN

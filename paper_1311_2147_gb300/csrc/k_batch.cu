@@ -18,17 +18,6 @@
 
 namespace bcg {
 
-// Graph g of task j: last g with off[g] <= j (off non-decreasing, off[0] = 0).
-__device__ __forceinline__ int graph_of(const int64_t* off, int G, int64_t j) {
-    int lo = 0, hi = G;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (off[mid] <= j) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // ---------------------------------------------------------------- E* writes
 
 __global__ void kb_estar(BatchArgs b, int r) {
@@ -79,6 +68,14 @@ __global__ void kb_vertex_pass(BatchArgs b, int r, int kind) {
                 dev_alg4_out<DT>(x, d.n, D, d.S, u.v, e, u.k, d.directed, (DT*)d.cD, d.cS, d.cM, d.changed, d.err);
                 break;
             default:
+                if (d.pair_on) {
+                    // row v is never written before this in an update: its changes are first changes
+                    PairRec rec = make_pair_rec(d);
+                    rec.first = 1;
+                    const size_t i = (size_t)u.v * d.n + x;
+                    if (D[i] != ((const DT*)d.cD)[x] || d.S[i] != d.cS[x])
+                        record_change<DT>(rec, d.n, u.v, x, D[i], d.S[i]);
+                }
                 dev_write_row<DT>(x, d.n, (DT*)d.D, d.S, u.v, (const DT*)d.cD, d.cS, d.err);
         }
     }
@@ -86,14 +83,15 @@ __global__ void kb_vertex_pass(BatchArgs b, int r, int kind) {
 
 // ---------------------------------------------------------------- compaction
 
-// which 0: IN-phase rows, 1: OUT-phase rows, 2: rows to re-accumulate (clears changed).
+// which 0: IN-phase rows, 1: OUT-phase rows, 2: rows to re-accumulate (clears changed;
+// graphs with pair corrections list theirs in kb_pair_lists).
 __global__ void __launch_bounds__(kCompactThreads) kb_compact(BatchArgs b, int r, int which) {
     for (int g = blockIdx.x; g < b.G; g += gridDim.x) {
         const BatchUpd u = b.upd[(int64_t)r * b.G + g];
         const Dev& d = b.devs[g];
         if (which == 0 && u.kin == 0) continue;
         if (which == 1 && u.kout == 0) continue;
-        if (which == 2 && u.present == 0) continue;
+        if (which == 2 && (u.present == 0 || d.pair_on)) continue;
         if (which < 2) dev_compact(d.n, d.mark, 0, d.rows, d.counts, 0, nullptr, d.err);
         else dev_compact(d.n, d.changed, 1, d.acc_rows, d.counts + 1, 0, d.stats, d.err);
         __syncthreads();
@@ -105,7 +103,9 @@ __global__ void __launch_bounds__(kCompactThreads) kb_compact(BatchArgs b, int r
 // Per-graph work known only on the device, as exclusive prefix offsets over graphs:
 // kind 0: scan items of the phase rows (rows x column chunks); 1: BC partial tasks
 // (column blocks x row blocks of the rows to re-accumulate); 2: sources to
-// re-accumulate.  One CTA.
+// re-accumulate; 3: rows listed for pair corrections; 4 + c: column-test weight of the
+// graphs whose columns per thread are of class c (and its piece counter back to zero).
+// One CTA.
 __global__ void __launch_bounds__(1024) kb_plan(BatchArgs b, int r, int kind, int phase_active, int64_t* out,
                                                 int scan_unroll) {
     __shared__ int64_t wsum[32];
@@ -126,9 +126,13 @@ __global__ void __launch_bounds__(1024) kb_plan(BatchArgs b, int r, int kind, in
                     v = (int64_t)d.counts[0] * ((d.n + cw - 1) / cw);
                     atomicAdd(reinterpret_cast<unsigned long long*>(d.stats + 6), (unsigned long long)d.counts[0]);
                 } else if (kind == 1) {
-                    v = (int64_t)((d.n + 255) / 256) * ((d.counts[1] + kRowsPerBlock - 1) / kRowsPerBlock);
-                } else {
-                    v = d.counts[1];
+                    v = (int64_t)((d.n + 255) / 256) * ((acc_list_count(d) + kRowsPerBlock - 1) / kRowsPerBlock);
+                } else if (kind == 2) {
+                    v = acc_list_count(d);
+                } else if (kind == 3) {
+                    v = d.pair_on ? d.counts[1] : 0;
+                } else if (d.pair_on && pair_class(d.dbytes, pair_vn(d.dbytes, d.n)) == kind - 4) {
+                    v = d.pair_w[d.counts[5]];
                 }
             }
         }
@@ -157,7 +161,10 @@ __global__ void __launch_bounds__(1024) kb_plan(BatchArgs b, int r, int kind, in
         if (threadIdx.x == 0) s_base += s_total;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[G] = s_base;
+    if (threadIdx.x == 0) {
+        out[G] = s_base;
+        if (kind >= 4) b.pctr[kind - 4] = 0;
+    }
 }
 
 // ---------------------------------------------------------------- rank-1 pass
@@ -177,7 +184,7 @@ __device__ __forceinline__ ScanArgs<DT> batch_scan_args(const Dev& d, const Batc
     a.stats = d.stats;
     a.tie_rows = 0;
     a.tie_cols = 0;
-    a.rec = PairRec{};   // the batched path re-accumulates every changed row
+    a.rec = d.pair_on ? make_pair_rec(d) : PairRec{};
     a.rows2 = nullptr;
     a.count2 = nullptr;
     a.cD2 = nullptr;
@@ -187,6 +194,7 @@ __device__ __forceinline__ ScanArgs<DT> batch_scan_args(const Dev& d, const Batc
         a.cS = d.S + (size_t)u.v * d.n;
         a.cM = a.cS;
         a.skip_row = -1;
+        a.rec.first = 1;   // the IN phase is the first pass of an update that writes pairs
     } else {
         a.cD = (const DT*)d.cD;
         a.cS = d.cS;
@@ -260,7 +268,7 @@ __global__ void kb_bc_partial(BatchArgs b, int r, const int64_t* off) {
         const int tb = (d.n + 255) / 256;
         const int rb = (int)(task / tb);
         const int t = (int)(task - (int64_t)rb * tb) * 256 + threadIdx.x;
-        dev_bc_partial(t, rb, d.n, d.acc_rows, d.counts[1], d.Dl, d.partial);
+        dev_bc_partial(t, rb, d.n, acc_list(d), acc_list_count(d), d.Dl, d.partial);
     }
 }
 
@@ -274,7 +282,7 @@ __global__ void kb_bc_finish(BatchArgs b, int r, double sign) {
         const Dev& d = b.devs[g];
         if (*d.err || b.upd[(int64_t)r * G + g].present == 0) continue;
         const int t = (int)(j - off[g]);
-        dev_bc_finish(t, d.n, d.counts[1], d.partial, sign, 0, d.bc_hi, d.bc_lo);
+        dev_bc_finish(t, d.n, acc_list_count(d), d.partial, sign, 0, d.bc_hi, d.bc_lo);
     }
 }
 
@@ -302,14 +310,14 @@ __global__ void __launch_bounds__(kAccThreadsNarrow) kb_accum(BatchArgs b, int r
         a.e_src = d.e_src;
         a.e_arc = (const Arc<DT>*)d.e_arc;
         a.e_cap = d.e_cap;
-        a.rows = d.acc_rows;
-        a.count = d.counts + 1;
+        a.rows = acc_list(d);
+        a.count = d.pair_on ? d.counts + 3 : d.counts + 1;
         a.ws = b.ws;
         a.ws_stride = b.ws_stride;
         a.err = d.err;
         a.mask_in_smem = b.mask_in_smem;
         const AccSmem m = acc_smem(a, smem, wsb);
-        dev_accum_source<DT, false, kAccThreadsNarrow>(a, d.acc_rows[j - off[g]], m, ls, &s_tail, &s_nbig);
+        dev_accum_source<DT, false, kAccThreadsNarrow>(a, a.rows[j - off[g]], m, ls, &s_tail, &s_nbig);
     }
 }
 
@@ -344,8 +352,11 @@ static void round_launches(const BatchArgs& b, const BatchLaunch& L, int r, cuda
     kb_plan<<<1, 1024, 0, st>>>(b, r, 0, 1, b.plan_scan, L.scan_unroll);
     batch_scan<DT>(b, L, r, 1, st);
     kb_vertex_pass<DT><<<nsm * L.vpass_ctas, 256, 0, st>>>(b, r, 3);
-    // rows to re-accumulate, BC minus the old rows, accumulation, BC plus the new rows
+    // rows to re-accumulate, BC minus the old rows, accumulation, BC plus the new rows;
+    // in graphs with pair corrections only the rows over the target cap, and the others
+    // are corrected pair by pair after (the order of the single-graph path)
     kb_compact<<<std::min(b.G, nsm * 2), kCompactThreads, 0, st>>>(b, r, 2);
+    if (L.pair_classes) batch_pair_lists(b, L, r, st);
     kb_plan<<<1, 1024, 0, st>>>(b, r, 1, 2, b.plan_bc, L.scan_unroll);
     kb_plan<<<1, 1024, 0, st>>>(b, r, 2, 2, b.plan_acc, L.scan_unroll);
     kb_bc_partial<<<nsm * L.bc_ctas, 256, 0, st>>>(b, r, b.plan_bc);
@@ -353,6 +364,12 @@ static void round_launches(const BatchArgs& b, const BatchLaunch& L, int r, cuda
     kb_accum<DT><<<L.acc_grid, kAccThreadsNarrow, L.acc_smem, st>>>(b, r, b.plan_acc);
     kb_bc_partial<<<nsm * L.bc_ctas, 256, 0, st>>>(b, r, b.plan_bc);
     kb_bc_finish<<<nsm * 2, 256, 0, st>>>(b, r, +1.0);
+    if (L.pair_classes) batch_pair_launches(b, L, r, sizeof(DT), st);
+}
+
+void batch_plan(const BatchArgs& b, int r, int kind, int phase_active, int64_t* out, int scan_unroll,
+                cudaStream_t st) {
+    kb_plan<<<1, 1024, 0, st>>>(b, r, kind, phase_active, out, scan_unroll);
 }
 
 void batch_config(BatchLaunch& L, int dbytes, int n_max, int64_t cap_max) {

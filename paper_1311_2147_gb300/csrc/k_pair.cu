@@ -18,6 +18,7 @@
 // saved values.  In G_D of an undirected graph d(x,t) = d(t,x) and sigma_xt = sigma_tx
 // before and after the update, so the column t of the formula is row t, read
 // contiguously.  Rows with more targets than the cap are re-accumulated by Algorithm 1.
+#include "bc_batch.cuh"
 #include "bc_device.cuh"
 #include "ff.cuh"
 
@@ -31,7 +32,6 @@ constexpr int kPairCtasPerSm = 4;
 // with eight (whose two loads per target already overlap)
 template <int VN> struct PairGroup { static constexpr int value = VN >= 8 ? 1 : 2; };
 constexpr int kPairPieces = 8;  // pieces of equal weight per CTA of the grid
-constexpr int kPairVec32 = 8;   // columns per thread with int32 distances (4 or 8)
 
 // The row lists of an update's corrections in one pass over the changed-row flags (one
 // CTA, kCompactPerThread flags per thread and tile, as k_compact): acc_rows = the
@@ -39,18 +39,15 @@ constexpr int kPairVec32 = 8;   // columns per thread with int32 distances (4 or
 // in full), both in increasing order.  The flags are cleared and the per-update counters
 // added as k_compact does for acc_rows.  A thread's two counts travel in one scan word
 // (each tile holds at most 1024 x 16 < 2^16 rows).
-__global__ void __launch_bounds__(kCompactThreads) k_pair_lists(int n, uint8_t* changed, const int32_t* tcnt,
-                                                                int tcap, int32_t* acc_rows, int32_t* acc_count,
-                                                                int32_t* full_rows, int32_t* full_count,
-                                                                int64_t* stats, const int32_t* err) {
-    pdl_enter();
+// (CTA-wide; wsum and s_total in shared memory.)
+__device__ __forceinline__ void dev_pair_lists(int n, uint8_t* changed, const int32_t* tcnt, int tcap,
+                                               int32_t* acc_rows, int32_t* acc_count, int32_t* full_rows,
+                                               int32_t* full_count, int64_t* stats, bool bad, int32_t* wsum,
+                                               int32_t& s_total) {
     constexpr int E = kCompactPerThread;
     static_assert(kCompactThreads * E < (1 << 16), "a tile's counts fit 16 bits");
-    __shared__ int32_t wsum[32];
-    __shared__ int32_t s_total;
     const int nwarps = blockDim.x >> 5;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool bad = *err != 0;
     int base_a = 0, base_f = 0;
     for (int tile = 0; tile < n; tile += (int)blockDim.x * E) {
         const int s0 = tile + tid * E;
@@ -118,28 +115,43 @@ __global__ void __launch_bounds__(kCompactThreads) k_pair_lists(int n, uint8_t* 
     }
 }
 
+__global__ void __launch_bounds__(kCompactThreads) k_pair_lists(int n, uint8_t* changed, const int32_t* tcnt,
+                                                                int tcap, int32_t* acc_rows, int32_t* acc_count,
+                                                                int32_t* full_rows, int32_t* full_count,
+                                                                int64_t* stats, const int32_t* err) {
+    pdl_enter();
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t s_total;
+    dev_pair_lists(n, changed, tcnt, tcap, acc_rows, acc_count, full_rows, full_count, stats, *err != 0, wsum,
+                   s_total);
+}
+
 // Per-update records of the rows listed in rows[0..count) back to zero (a pair (s,t)
 // changes only in a changed row s), a warp per row: a row with at most tcap changed
 // targets has its bits only in the words of its listed targets, a longer one is
 // cleared whole.  The rows sent to the full path are added to stats[7].
+__device__ __forceinline__ void dev_pair_clear_row(int s, int32_t* tcnt, const int32_t* tlist, int tcap,
+                                                   uint32_t* chg, int words) {
+    const int lane = threadIdx.x & 31;
+    const int T = tcnt[s];
+    uint32_t* row = chg + (size_t)s * words;
+    if (T <= tcap) {
+        for (int j = lane; j < T; j += 32) row[tlist[(size_t)s * tcap + j] >> 5] = 0u;
+    } else {
+        for (int j = lane; j < words; j += 32) row[j] = 0u;
+    }
+    __syncwarp();
+    if (lane == 0) tcnt[s] = 0;
+}
+
 __global__ void k_pair_clear(const int32_t* rows, const int32_t* count, int32_t* tcnt, const int32_t* tlist,
                              int tcap, uint32_t* chg, int words, const int32_t* full_count, int64_t* stats) {
     pdl_enter();
     const int cnt = *count;
     if (blockIdx.x == 0 && threadIdx.x == 0) stats[7] += *full_count;
-    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < cnt; i += gridDim.x * wpb) {
-        const int s = rows[i];
-        const int T = tcnt[s];
-        uint32_t* row = chg + (size_t)s * words;
-        if (T <= tcap) {
-            for (int j = lane; j < T; j += 32) row[tlist[(size_t)s * tcap + j] >> 5] = 0u;
-        } else {
-            for (int j = lane; j < words; j += 32) row[j] = 0u;
-        }
-        __syncwarp();
-        if (lane == 0) tcnt[s] = 0;
-    }
+    const int wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < cnt; i += gridDim.x * wpb)
+        dev_pair_clear_row(rows[i], tcnt, tlist, tcap, chg, words);
 }
 
 // One changed target t of a row s, as prepared by k_pair_plan: the pair's distance and
@@ -207,41 +219,44 @@ __device__ __forceinline__ void bc_fix_add(int64_t* fix, int x, ff v) {
 // plan.  Every target of row s has its bit set, so its old values are the saved ones.
 constexpr int kPlanThreads = 256;
 
+// (One warp; sv: kPairCap ints of shared memory.)
+template <typename DT>
+__device__ __forceinline__ void dev_pair_plan_row(const PairArgs<DT>& a, int s, int32_t* sv) {
+    const int n = a.n;
+    const int64_t INF = Inf<DT>::v;
+    const int lane = threadIdx.x & 31;
+    const int T = a.tcnt[s];
+    if (T == 0 || T > a.tcap) return;   // warp-uniform
+    for (int j = lane; j < T; j += 32) sv[j] = a.tlist[(size_t)s * a.tcap + j];
+    __syncwarp();
+    for (int j = lane; j < T; j += 32) {
+        const int val = sv[j];
+        int pos = 0;
+        for (int k = 0; k < T; ++k) pos += sv[k] < val;   // targets are distinct
+        const size_t it = (size_t)s * n + val;
+        const int64_t dol = a.oD[it], dnw = a.D[it];
+        const uint64_t sol = a.oS[it], snw = a.S[it];
+        PairTgt p;
+        p.t = val;
+        p.pad = 0;
+        p.dold = (dol == INF || sol == 0) ? -1 : dol;
+        p.dnew = (dnw == INF || snw == 0) ? -1 : dnw;
+        p.rold = sol ? ff_rcp(ff_from_u64(sol)) : ff{0.f, 0.f};
+        p.rnew = snw ? ff_rcp(ff_from_u64(snw)) : ff{0.f, 0.f};
+        a.plan[(size_t)s * a.tcap + pos] = p;
+    }
+    __syncwarp();
+}
+
 template <typename DT>
 __global__ void __launch_bounds__(kPlanThreads) k_pair_plan(PairArgs<DT> a) {
     pdl_enter();
     __shared__ int32_t s_val[kPlanThreads / 32][kPairCap];
     if (*a.err) return;
-    const int n = a.n;
-    const int64_t INF = Inf<DT>::v;
     const int cnt = *a.count;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int32_t* sv = s_val[wib];
+    const int wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (kPlanThreads / 32);
-    for (int i = blockIdx.x * (kPlanThreads / 32) + wib; i < cnt; i += nw) {
-        const int s = a.rows[i];
-        const int T = a.tcnt[s];
-        if (T == 0 || T > a.tcap) continue;   // warp-uniform
-        for (int j = lane; j < T; j += 32) sv[j] = a.tlist[(size_t)s * a.tcap + j];
-        __syncwarp();
-        for (int j = lane; j < T; j += 32) {
-            const int val = sv[j];
-            int pos = 0;
-            for (int k = 0; k < T; ++k) pos += sv[k] < val;   // targets are distinct
-            const size_t it = (size_t)s * n + val;
-            const int64_t dol = a.oD[it], dnw = a.D[it];
-            const uint64_t sol = a.oS[it], snw = a.S[it];
-            PairTgt p;
-            p.t = val;
-            p.pad = 0;
-            p.dold = (dol == INF || sol == 0) ? -1 : dol;
-            p.dnew = (dnw == INF || snw == 0) ? -1 : dnw;
-            p.rold = sol ? ff_rcp(ff_from_u64(sol)) : ff{0.f, 0.f};
-            p.rnew = snw ? ff_rcp(ff_from_u64(snw)) : ff{0.f, 0.f};
-            a.plan[(size_t)s * a.tcap + pos] = p;
-        }
-        __syncwarp();
-    }
+    for (int i = blockIdx.x * (kPlanThreads / 32) + wib; i < cnt; i += nw) dev_pair_plan_row<DT>(a, a.rows[i], s_val[wib]);
 }
 
 // sigma_sx * sigma_xt / sigma_st in float-float (the quotient as a product with the
@@ -336,17 +351,23 @@ __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0
 // bucket with one shared-memory atomic), then each warp scans a contiguous run of the
 // sorted rows and one block scan joins the runs.
 // Also adds the rows with a correction and their targets to stats[8], stats[9].
-__global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
-                                                       const int32_t* tcnt, int tcap, int nchunks,
-                                                       int32_t* prows, int32_t* pcount,
-                                                       int64_t* wpre, int64_t* stats, int32_t* next_piece,
-                                                       int32_t* walk_ctl, int32_t* walk_rowE, const int32_t* err) {
-    pdl_enter();
-    __shared__ int64_t wsum[32];
-    __shared__ int64_t s_total;
-    __shared__ int64_t s_rows[32], s_tgts[32];
-    __shared__ int s_hist[kPairCap + 1];
-    if (*err) return;
+struct PairWeightsSmem {
+    int64_t wsum[32];
+    int64_t s_total;
+    int64_t s_rows[32], s_tgts[32];
+    int s_hist[kPairCap + 1];
+};
+
+// (CTA-wide, 1024 threads.)
+__device__ __forceinline__ void dev_pair_weights(const int32_t* rows, const int32_t* count, const int32_t* tcnt,
+                                                 int tcap, int nchunks, int32_t* prows, int32_t* pcount,
+                                                 int64_t* wpre, int64_t* stats, int32_t* next_piece,
+                                                 int32_t* walk_ctl, int32_t* walk_rowE, PairWeightsSmem& sm) {
+    int64_t* wsum = sm.wsum;
+    int64_t& s_total = sm.s_total;
+    int64_t* s_rows = sm.s_rows;
+    int64_t* s_tgts = sm.s_tgts;
+    int* s_hist = sm.s_hist;
     const int cnt_all = *count;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = blockDim.x >> 5;
@@ -454,6 +475,18 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
         stats[8] += r;
         stats[9] += t;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, const int32_t* count,
+                                                       const int32_t* tcnt, int tcap, int nchunks,
+                                                       int32_t* prows, int32_t* pcount,
+                                                       int64_t* wpre, int64_t* stats, int32_t* next_piece,
+                                                       int32_t* walk_ctl, int32_t* walk_rowE, const int32_t* err) {
+    pdl_enter();
+    __shared__ PairWeightsSmem sm;
+    if (*err) return;
+    dev_pair_weights(rows, count, tcnt, tcap, nchunks, prows, pcount, wpre, stats, next_piece, walk_ctl, walk_rowE,
+                     sm);
 }
 
 // Queue of one warp's matches: entry = lane (5 bits) | q (3) | target index u (7) |
@@ -698,11 +731,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) k_pairdep(PairAr
 // next update: B's high bits are carried into A (A' = A + (B >> 32), B' = B mod 2^32),
 // so A' * 2^-24 and B' * 2^-56 are exact doubles, added with TwoSum as in
 // dev_bc_finish.
-__global__ void k_bc_fix(int n, int64_t* fix, double* hi, double* lo, const int32_t* err) {
-    pdl_enter();
-    if (*err) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+__device__ __forceinline__ void dev_bc_fix(int t, int64_t* fix, double* hi, double* lo) {
     const longlong2 f = *reinterpret_cast<const longlong2*>(fix + 2 * (size_t)t);
     if (f.x == 0 && f.y == 0) return;
     *reinterpret_cast<longlong2*>(fix + 2 * (size_t)t) = make_longlong2(0, 0);
@@ -718,20 +747,16 @@ __global__ void k_bc_fix(int n, int64_t* fix, double* hi, double* lo, const int3
     lo[t] += e + x2;
 }
 
+__global__ void k_bc_fix(int n, int64_t* fix, double* hi, double* lo, const int32_t* err) {
+    pdl_enter();
+    if (*err) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dev_bc_fix(t, fix, hi, lo);
+}
+
 // ------------------------------------------------------------------ launches
 
-PairRec pair_rec(const Dev& d) {
-    PairRec r;
-    r.chg = d.chg;
-    r.chg_words = d.chg_words;
-    r.oldD = d.oldD;
-    r.oldS = d.oldS;
-    r.tcnt = d.tcnt;
-    r.tlist = d.tlist;
-    r.tcap = d.tcap;
-    r.first = 0;
-    return r;
-}
+PairRec pair_rec(const Dev& d) { return make_pair_rec(d); }
 
 void launch_pair_lists(const Dev& d) {
     launch_k(k_pair_lists, 1, kCompactThreads, 0, d.st, d.n, d.changed, d.tcnt, d.tcap, d.acc_rows, d.counts + 1,
@@ -744,7 +769,7 @@ void launch_pair_clear(const Dev& d) {
 }
 
 template <typename DT>
-static PairArgs<DT> pair_args(const Dev& d) {
+__host__ __device__ inline PairArgs<DT> pair_args(const Dev& d) {
     PairArgs<DT> a;
     a.n = d.n;
     a.D = (const DT*)d.D;
@@ -768,6 +793,222 @@ static PairArgs<DT> pair_args(const Dev& d) {
     a.bcfix = d.bcfix;
     a.err = d.err;
     return a;
+}
+
+// ------------------------------------------------------------------ batches
+//
+// The pair corrections of round r of a batch, for every graph that has them (the rest of
+// the round is in k_batch.cu).  Each kernel runs the single-graph kernel's device
+// function on the concatenated work of all graphs, a task mapped to its graph by binary
+// search over prefix offsets, so a graph's result in a batch is bit-identical to its
+// result alone.  The column test always serves a batch (the DAG walks are for graphs far
+// larger than a batch's).
+
+__device__ __forceinline__ bool batch_pair_graph(const BatchArgs& b, int r, int g) {
+    const Dev& d = b.devs[g];
+    return d.pair_on && b.upd[(int64_t)r * b.G + g].present && *d.err == 0;
+}
+
+// One CTA per graph in turn: the row lists of its corrections (k_pair_lists).
+__global__ void __launch_bounds__(kCompactThreads) kb_pair_lists(BatchArgs b, int r) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t s_total;
+    for (int g = blockIdx.x; g < b.G; g += gridDim.x) {
+        const Dev& d = b.devs[g];
+        if (!d.pair_on || b.upd[(int64_t)r * b.G + g].present == 0) continue;   // block-uniform
+        dev_pair_lists(d.n, d.changed, d.tcnt, d.tcap, d.acc_rows, d.counts + 1, d.full_rows, d.counts + 3, d.stats,
+                       *d.err != 0, wsum, s_total);
+        __syncthreads();
+    }
+}
+
+// A warp per listed row of every graph (k_pair_plan); plan_pr offsets the rows.
+template <typename DT>
+__global__ void __launch_bounds__(kPlanThreads) kb_pair_plan(BatchArgs b) {
+    __shared__ int32_t s_val[kPlanThreads / 32][kPairCap];
+    const int G = b.G;
+    const int64_t total = b.plan_pr[G];
+    const int wib = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (kPlanThreads / 32);
+    for (int64_t j = (int64_t)blockIdx.x * (kPlanThreads / 32) + wib; j < total; j += nw) {
+        const int g = graph_of(b.plan_pr, G, j);
+        const Dev& d = b.devs[g];
+        const PairArgs<DT> a = pair_args<DT>(d);
+        dev_pair_plan_row<DT>(a, d.acc_rows[j - b.plan_pr[g]], s_val[wib]);
+    }
+}
+
+// One CTA per graph in turn: rows most targets first and their weight prefix
+// (k_pair_weights), with the graph's own columns per thread.
+__global__ void __launch_bounds__(1024) kb_pair_weights(BatchArgs b, int r) {
+    __shared__ PairWeightsSmem sm;
+    for (int g = blockIdx.x; g < b.G; g += gridDim.x) {
+        if (!batch_pair_graph(b, r, g)) continue;   // block-uniform
+        const Dev& d = b.devs[g];
+        const int cw = kPairThreads * pair_vn(d.dbytes, d.n);
+        const int nchunks = (d.n + cw - 1) / cw;
+        dev_pair_weights(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows, d.counts + 5, d.pair_w,
+                         d.stats, d.counts + 4, nullptr, nullptr, sm);
+        __syncthreads();
+    }
+}
+
+// The column test (k_pairdep) over the graphs whose columns per thread are VN: their
+// weight lines laid end to end (plan_pw of the class), cut into kPairPieces x grid pieces
+// of equal weight; a piece runs the items whose start falls in it, across row and graph
+// boundaries, and later pieces go to the CTAs that finish first (counter pctr).
+template <typename DT, int VN>
+__global__ void __launch_bounds__(kPairThreads, kPairCtasPerSm) kb_pairdep(BatchArgs b, int cls) {
+    __shared__ TgtFast<DT> s_fa[kPairCap];
+    __shared__ TgtSlow s_sl[kPairCap];
+    __shared__ ff s_acc[VN][kPairThreads];
+    __shared__ PairQueue s_wq[kPairThreads / 32];
+    __shared__ int s_g, s_i, s_c, s_p;
+    constexpr int CW = kPairThreads * VN;
+    const int G = b.G;
+    const int64_t* off = b.plan_pw + (int64_t)cls * (G + 1);
+    const int64_t W = off[G];
+    const int npieces = gridDim.x * kPairPieces;
+    int cg = -1;                     // the graph whose arguments are loaded
+    int sg = -1, cur = -1, s = -1;   // the graph and row whose plan is staged
+    int U_ = 0, nchunks = 1, cnt = 0;
+    PairArgs<DT> a{};
+    for (int piece = blockIdx.x; piece < npieces;) {
+        const int64_t lo = W * piece / npieces, hi = W * (piece + 1) / npieces;
+        if (lo < hi) {   // block-uniform
+            if (threadIdx.x == 0) {
+                // the graph holding lo (off[g] <= lo < off[g + 1]), then its last row whose
+                // items start at or before lo
+                const int g = graph_of(off, G, lo);
+                const Dev& d = b.devs[g];
+                const int nch = (d.n + CW - 1) / CW;
+                const int64_t l = lo - off[g];
+                int L = 0, R = d.counts[5];
+                while (R - L > 1) {
+                    const int m = (L + R) >> 1;
+                    if (d.pair_w[m] <= l) L = m; else R = m;
+                }
+                const int64_t wc = (d.pair_w[L + 1] - d.pair_w[L]) / nch;   // > 0: l lies in row L
+                s_g = g;
+                s_i = L;
+                s_c = (int)((l - d.pair_w[L] + wc - 1) / wc);
+            }
+            __syncthreads();
+            int g = s_g, i = s_i, c = s_c;
+            if (g != cg) {
+                cg = g;
+                a = pair_args<DT>(b.devs[g]);
+                nchunks = (a.n + CW - 1) / CW;
+                cnt = *a.pcount;
+            }
+            int64_t wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
+            for (;;) {
+                if (c >= nchunks) {   // next row with items, in this graph or the next ones (block-uniform)
+                    do {
+                        ++i;
+                    } while (i < cnt && a.wpre[i + 1] == a.wpre[i]);
+                    while (i >= cnt) {
+                        do {
+                            ++g;
+                        } while (g < G && off[g + 1] == off[g]);
+                        if (g >= G) break;
+                        cg = g;
+                        a = pair_args<DT>(b.devs[g]);
+                        nchunks = (a.n + CW - 1) / CW;
+                        cnt = *a.pcount;
+                        i = 0;
+                        while (i < cnt && a.wpre[i + 1] == a.wpre[i]) ++i;
+                    }
+                    if (g >= G) break;
+                    wc = (a.wpre[i + 1] - a.wpre[i]) / nchunks;
+                    c = 0;
+                }
+                if (off[g] + a.wpre[i] + (int64_t)c * wc >= hi) break;
+                if (i != cur || g != sg) {
+                    cur = i;
+                    sg = g;
+                    s = a.prows[i];
+                    U_ = (int)wc - 1;
+                    __syncthreads();   // the previous row's plan is no longer read
+                    if (threadIdx.x < U_) {
+                        const PairTgt p = a.plan[(size_t)s * a.tcap + threadIdx.x];
+                        const size_t rt = (size_t)p.t * a.n;
+                        s_fa[threadIdx.x] =
+                            TgtFast<DT>{a.D + rt, a.chg + (size_t)p.t * a.words, (DT)p.dold, (DT)p.dnew};
+                        s_sl[threadIdx.x] = TgtSlow{(int64_t)rt, p.rold, p.rnew};
+                    }
+                    __syncthreads();
+                }
+                const int x0 = c * CW + threadIdx.x * VN;
+                ++c;
+                if (x0 - (int)(threadIdx.x & 31) * VN < a.n)
+                    pair_item<DT, VN>(a, s, U_, x0, s_fa, s_sl, s_acc, s_wq[threadIdx.x >> 5]);
+            }
+        }
+        if (threadIdx.x == 0) s_p = gridDim.x + atomicAdd(b.pctr + cls, 1);
+        __syncthreads();
+        piece = s_p;
+        __syncthreads();
+    }
+}
+
+// BC += the fixed-point change of each column of every graph with corrections (k_bc_fix).
+__global__ void kb_bc_fix(BatchArgs b, int r) {
+    const int G = b.G;
+    const int64_t total = b.coff[G];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int g = graph_of(b.coff, G, j);
+        if (!batch_pair_graph(b, r, g)) continue;
+        const Dev& d = b.devs[g];
+        dev_bc_fix((int)(j - b.coff[g]), d.bcfix, d.bc_hi, d.bc_lo);
+    }
+}
+
+// The per-update records back to zero, a warp per listed row (k_pair_clear).
+__global__ void kb_pair_clear(BatchArgs b, int r) {
+    const int G = b.G;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        if (batch_pair_graph(b, r, g)) b.devs[g].stats[7] += b.devs[g].counts[3];
+    const int64_t total = b.plan_pr[G];
+    const int wpb = blockDim.x >> 5;
+    for (int64_t j = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); j < total; j += (int64_t)gridDim.x * wpb) {
+        const int g = graph_of(b.plan_pr, G, j);
+        const Dev& d = b.devs[g];
+        dev_pair_clear_row(d.acc_rows[j - b.plan_pr[g]], d.tcnt, d.tlist, d.tcap, d.chg, d.chg_words);
+    }
+}
+
+void batch_pair_lists(const BatchArgs& b, const BatchLaunch& L, int r, cudaStream_t st) {
+    kb_pair_lists<<<std::min(b.G, L.nsm * 2), kCompactThreads, 0, st>>>(b, r);
+}
+
+template <typename DT>
+static void batch_pairs(const BatchArgs& b, const BatchLaunch& L, int r, cudaStream_t st) {
+    const int G = b.G, nsm = L.nsm;
+    batch_plan(b, r, 3, 2, b.plan_pr, L.scan_unroll, st);
+    kb_pair_plan<DT><<<nsm * 8, kPlanThreads, 0, st>>>(b);
+    kb_pair_weights<<<std::min(G, nsm * 2), 1024, 0, st>>>(b, r);
+    const int pgrid = nsm * kPairCtasPerSm;
+    for (int c = 0; c < kPairClasses; ++c) {
+        if (!((L.pair_classes >> c) & 1)) continue;
+        batch_plan(b, r, 4 + c, 2, b.plan_pw + (int64_t)c * (G + 1), L.scan_unroll, st);
+        if constexpr (sizeof(DT) == 4) {
+            if (c == 0) kb_pairdep<DT, 8><<<pgrid, kPairThreads, 0, st>>>(b, c);
+            else if (c == 1) kb_pairdep<DT, 4><<<pgrid, kPairThreads, 0, st>>>(b, c);
+            else kb_pairdep<DT, 1><<<pgrid, kPairThreads, 0, st>>>(b, c);
+        } else {
+            if (c == 0) kb_pairdep<DT, 2><<<pgrid, kPairThreads, 0, st>>>(b, c);
+            else kb_pairdep<DT, 1><<<pgrid, kPairThreads, 0, st>>>(b, c);
+        }
+    }
+    kb_bc_fix<<<nsm * 4, 256, 0, st>>>(b, r);
+    kb_pair_clear<<<nsm * 4, 256, 0, st>>>(b, r);
+}
+
+void batch_pair_launches(const BatchArgs& b, const BatchLaunch& L, int r, int dbytes, cudaStream_t st) {
+    if (dbytes == 4) batch_pairs<int32_t>(b, L, r, st);
+    else batch_pairs<int64_t>(b, L, r, st);
 }
 
 // ------------------------------------------------------------------ DAG walks
@@ -1239,8 +1480,7 @@ void launch_pairdep(const Dev& d, const WalkUpd* upd) {
     if (d.dbytes == 4) launch_k(k_pair_plan<int32_t>, pgrid, kPlanThreads, 0, d.st, pair_args<int32_t>(d));
     else launch_k(k_pair_plan<int64_t>, pgrid, kPlanThreads, 0, d.st, pair_args<int64_t>(d));
     // columns per thread: 16-byte (or two 16-byte) loads where n allows them
-    const int vn = (d.dbytes == 4) ? ((kPairVec32 == 8 && d.n % 8 == 0) ? 8 : (d.n % 4 == 0 ? 4 : 1))
-                                   : (d.n % 2 == 0 ? 2 : 1);
+    const int vn = pair_vn(d.dbytes, d.n);
     const int cw = kPairThreads * vn;
     const int nchunks = (d.n + cw - 1) / cw;
     launch_k(k_pair_weights, 1, 1024, 0, d.st, d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows,

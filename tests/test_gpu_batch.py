@@ -35,18 +35,23 @@ def _family(count, seed, nlo=40, nhi=400, vertex=True):
     return out
 
 
-def test_batch_equals_alone_and_oracle():
+@pytest.mark.parametrize("pairs", [1, 0], ids=["pair-corrections", "full-reaccumulation"])
+def test_batch_equals_alone_and_oracle(pairs):
+    # undirected graphs: pair corrections (the default) or every changed row
+    # re-accumulated, the same option on the handles alone and in the batch
     fam = _family(12, 77)
     alone = []
     for g, ups in fam:
         a = binding.BCGraph(g)
         if not g.directed:
-            # the batched path re-accumulates every changed row; so must the handle
-            a.bc_set_option("pair_updates", 0)
+            a.bc_set_option("pair_updates", pairs)
         rc, done = a.bc_apply_updates(ups)
         assert rc == 0 and done == len(ups)
         alone.append(a)
     mixed = [binding.BCGraph(g) for g, _ in fam]
+    for m in mixed:
+        if not m.directed:
+            m.bc_set_option("pair_updates", pairs)
     batch = binding.BCBatch(mixed)
     rc, done = batch.bc_batch_apply([ups for _, ups in fam])
     assert rc == 0, batch.last_error()
@@ -56,6 +61,9 @@ def test_batch_equals_alone_and_oracle():
             assert np.array_equal(x, y)
         assert np.array_equal(a.bc_get_scores(), m.bc_get_scores())
         compare_full(m, synth.apply_updates(g, ups), label=f"batch n={g.n}")
+    if pairs:
+        info = [m.bc_get_info() for (g, _), m in zip(fam, mixed) if not g.directed]
+        assert sum(i["pair_rows"] for i in info) > 0
 
 
 def test_batch_uneven_counts_and_repeat_calls():
