@@ -607,7 +607,10 @@ def run_batch(args):
     def next_step():
         k = step_i[0]
         step_i[0] += 1
-        return [ups[k * per:(k + 1) * per] for _, ups in fam]
+        lists = [ups[k * per:(k + 1) * per] for _, ups in fam]
+        if any(len(u) != per for u in lists):
+            raise RuntimeError(f"batch step {k} is past the generated stream ({total_steps} steps)")
+        return lists
 
     n_max = max(g.n for g, _ in fam)
     key = autotune.cache_key(len(fam), n_max, "i32")

@@ -262,7 +262,7 @@ int bc_get_profile(bc_graph* g, double* ms, int64_t* launches, int32_t reset);
  *                     results bit for bit.
  *   "wide_accum" 0|1 (on by default): on graphs of at least 4096 vertices, re-run
  *                     Algorithm 1 for the rows over the target cap in 1024-thread CTAs
- *                     (one source's passes spread over more threads); 0: 512-thread
+ *                     (one source's passes spread over more threads); 0: 256-thread
  *                     CTAs, which share SMs better with other handles' work (the server
  *                     sets 0 for its graphs).  Same results bit for bit.
  *   "pair_walk" 0|1 (undirected graphs only; BC_ERR_ARG on a directed graph): find the
@@ -370,7 +370,10 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
  * fit); with count >= 6 also the rank-1 pass's tile and schedule: tiles[4] 16-byte
  * vectors per thread per work item (1, 2, 4 or 8: the item's column chunk is 256
  * threads x tiles[4] x 16 bytes), tiles[5] 0 = a contiguous block of items per CTA,
- * 1 = items dealt out to the CTAs in turn.  The next bc_batch_apply captures a new CUDA graph. */
+ * 1 = items dealt out to the CTAs in turn; with count >= 7 also tiles[6] the threads of an
+ * accumulation CTA (512, 256 or 128: one source per CTA either way, more sources in flight
+ * per SM with fewer threads; same results bit for bit).  BC_ERR_ARG for a value out of range.
+ * The next bc_batch_apply captures a new CUDA graph. */
 int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count);
 
 /* bc_batch_last_ms -- device time (CUDA events around the graph launch) of the last apply. */

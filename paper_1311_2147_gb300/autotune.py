@@ -2,8 +2,9 @@
 
 The tunable shape is (CTAs per SM of the per-vertex passes, of the rank-1 pass, of the
 BC row sums, cap on accumulation CTAs per SM, the rank-1 pass's tile -- 16-byte vectors
-per thread per work item, so its column chunk -- and its schedule -- contiguous item
-blocks per CTA or items dealt out in turn).  The tuner runs coordinate descent from a
+per thread per work item, so its column chunk -- its schedule -- contiguous item
+blocks per CTA or items dealt out in turn -- and the threads of an accumulation CTA,
+512, 256 or 128).  The tuner runs coordinate descent from a
 default: for each parameter in turn it applies one batch step with every candidate value
 (each step consumes the next updates of the caller's stream, so the graphs advance as
 they would anyway) and keeps the fastest.  Results are cached in
@@ -17,8 +18,8 @@ import os
 
 from . import build as _build
 
-DEFAULT = [4, 8, 8, 0, 4, 0]
-CANDIDATES = [[2, 4, 8], [4, 8, 16], [4, 8, 16], [0, 1], [1, 2, 4, 8], [0, 1]]
+DEFAULT = [4, 8, 8, 0, 4, 0, 256]
+CANDIDATES = [[2, 4, 8], [4, 8, 16], [4, 8, 16], [0, 1], [1, 2, 4, 8], [0, 1], [512, 256, 128]]
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 TIMED_STEPS = 2   # timed batch steps per candidate (after one untimed step that captures the graph)
 
@@ -80,8 +81,9 @@ def tune(batch, next_step, key: str | None = None, use_cache: bool = True):
 
     best_ms = run(best)
     for i, values in enumerate(CANDIDATES):
+        incumbent = best[i]   # already timed: every other value of this parameter is run once
         for v in values:
-            if v == best[i]:
+            if v == incumbent:
                 continue
             cand = list(best)
             cand[i] = v

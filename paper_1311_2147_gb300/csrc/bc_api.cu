@@ -1137,7 +1137,7 @@ int bc_set_option(bc_graph* g, const char* name, int64_t value) {
     }
     if (std::strcmp(name, "wide_accum") == 0) {
         // 1024-thread accumulation CTAs for the rows over the target cap (graphs of at
-        // least 4096 vertices); 0: 512-thread ones, which share SMs better with the work of
+        // least 4096 vertices); 0: 256-thread ones, which share SMs better with the work of
         // other handles running at the same time (the server turns them off)
         g->d.acc_narrow_only = value != 0 ? 0 : 1;
         g->d.acc_threads = (value != 0 && g->n >= kAccWideMinN) ? kAccThreadsWide : kAccThreadsNarrow;
@@ -1320,6 +1320,7 @@ int bc_batch_create(bc_batch** out, int32_t count, bc_graph* const* graphs, void
     b->L.acc_per_sm = 0;
     b->L.scan_unroll = 4;   // the single-graph item width (kScanUnroll)
     b->L.scan_sched = 0;
+    b->L.acc_threads = kAccThreadsNarrow;
     int rc;
     if ((rc = balloc(b, &b->d_devs, count)) || (rc = balloc(b, &b->d_coff, count + 1)) ||
         (rc = balloc(b, &b->d_plans, (4 + (size_t)kPairClasses) * ((size_t)count + 1))) ||
@@ -1347,6 +1348,8 @@ int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count) {
     if (count >= 6 && ((tiles[4] != 1 && tiles[4] != 2 && tiles[4] != 4 && tiles[4] != 8) ||
                        (tiles[5] != 0 && tiles[5] != 1)))
         return bfail(b, BC_ERR_ARG, "rank-1 chunk (1, 2, 4, 8) or schedule (0, 1) out of range");
+    if (count >= 7 && tiles[6] != 128 && tiles[6] != 256 && tiles[6] != 512)
+        return bfail(b, BC_ERR_ARG, "accumulation CTA threads must be 128, 256 or 512");
     b->L.vpass_ctas = tiles[0];
     b->L.scan_ctas = tiles[1];
     b->L.bc_ctas = tiles[2];
@@ -1355,6 +1358,7 @@ int bc_batch_set_tiles(bc_batch* b, const int32_t* tiles, int32_t count) {
         b->L.scan_unroll = tiles[4];
         b->L.scan_sched = tiles[5];
     }
+    if (count >= 7) b->L.acc_threads = tiles[6];
     b->cap_max = -1;   // forces a new launch configuration
     drop_exec(b);
     return BC_OK;

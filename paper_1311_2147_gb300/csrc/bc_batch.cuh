@@ -62,6 +62,8 @@ struct BatchLaunch {
                           // chunk is 256 threads x this x the vector width (1, 2, 4, 8; tunable)
     int32_t scan_sched;   // 0: a contiguous block of items per CTA; 1: items dealt out in
                           // turn (item = CTA + k * grid)                (tunable)
+    int32_t acc_threads;  // threads of an accumulation CTA: 512, 256 or 128 (more sources
+                          // in flight per SM)                           (tunable)
     int32_t pair_classes; // bit c: some graph of the batch has pair corrections with columns
                           // per thread of class c (0: none; the round skips the pair kernels)
     int32_t acc_grid;

@@ -221,10 +221,11 @@ struct Dev {
 constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction
 // Threads of an accumulation CTA (one source at a time): 1024 for the few rows over the
 // target cap of an update on graphs of at least kAccWideMinN vertices (the level passes
-// of one source spread over more threads), 512 otherwise (two sources in flight per SM);
-// the batched path uses 512.
+// of one source spread over more threads), 256 otherwise (four sources in flight per SM:
+// saturated serving of 64 graphs 1783 -> 2028 updates/s against 512 threads, 128 threads
+// 1843); the batched path picks 128, 256 or 512 by autotuning.
 constexpr int kAccThreadsWide = 1024;
-constexpr int kAccThreadsNarrow = 512;
+constexpr int kAccThreadsNarrow = 256;
 constexpr int kAccWideMinN = 4096;
 
 // Accumulation launch shape for n and the current E* capacity (sets acc_grid, acc_smem,

@@ -179,10 +179,11 @@ static void accum_t(const Dev& d, int is_static, const int32_t* rows, const int3
 
 // The wide CTAs serve a partial wave of sources (the rows over the target cap of an
 // update with pair corrections: tens per update), where one source's latency is the
-// time (BA n = 16384: 0.30 ms per update wide, 0.41 ms narrow), and the static
-// computation on the largest graphs (n = 16384: 139 ms wide, 141 ms narrow; n = 8192:
-// 33.7 ms wide, 30.5 ms narrow).  Every changed row of an update without pair
-// corrections (thousands of sources) is served faster by the narrow ones, two per SM.
+// time (BA n = 16384: 0.30 ms per update wide, 0.41 ms with 512-thread CTAs), and the
+// static computation on the largest graphs (n = 16384: 139 ms wide, 141 ms with 512
+// threads; n = 8192: 33.7 ms wide, 30.5 ms with 512 threads, 30.3 ms with 256).  Every
+// changed row of an update without pair corrections (thousands of sources) is served
+// faster by the narrow ones, several per SM.
 constexpr int kAccStaticWideMinN = 16384;
 
 static void accum(const Dev& d, int is_static, const int32_t* rows, const int32_t* count) {

@@ -288,10 +288,12 @@ __global__ void kb_bc_finish(BatchArgs b, int r, double sign) {
 
 // ---------------------------------------------------------------- accumulation
 
-template <typename DT>
-__global__ void __launch_bounds__(kAccThreadsNarrow) kb_accum(BatchArgs b, int r, const int64_t* off) {
+// One source per CTA of T threads (128, 256 or 512: a tile the autotuner picks), held to
+// 64 registers so that 1024 threads share an SM.
+template <typename DT, int T>
+__global__ void __launch_bounds__(T, 1024 / T) kb_accum(BatchArgs b, int r, const int64_t* off) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ LevelSmem<kAccThreadsNarrow> ls;
+    __shared__ LevelSmem<T> ls;
     __shared__ int s_tail, s_nbig;
     const int G = b.G;
     const int64_t total = off[G];
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(kAccThreadsNarrow) kb_accum(BatchArgs b, int r
         a.err = d.err;
         a.mask_in_smem = b.mask_in_smem;
         const AccSmem m = acc_smem(a, smem, wsb);
-        dev_accum_source<DT, false, kAccThreadsNarrow>(a, a.rows[j - off[g]], m, ls, &s_tail, &s_nbig);
+        dev_accum_source<DT, false, T>(a, a.rows[j - off[g]], m, ls, &s_tail, &s_nbig);
     }
 }
 
@@ -361,7 +363,9 @@ static void round_launches(const BatchArgs& b, const BatchLaunch& L, int r, cuda
     kb_plan<<<1, 1024, 0, st>>>(b, r, 2, 2, b.plan_acc, L.scan_unroll);
     kb_bc_partial<<<nsm * L.bc_ctas, 256, 0, st>>>(b, r, b.plan_bc);
     kb_bc_finish<<<nsm * 2, 256, 0, st>>>(b, r, -1.0);
-    kb_accum<DT><<<L.acc_grid, kAccThreadsNarrow, L.acc_smem, st>>>(b, r, b.plan_acc);
+    if (L.acc_threads == 128) kb_accum<DT, 128><<<L.acc_grid, 128, L.acc_smem, st>>>(b, r, b.plan_acc);
+    else if (L.acc_threads == 256) kb_accum<DT, 256><<<L.acc_grid, 256, L.acc_smem, st>>>(b, r, b.plan_acc);
+    else kb_accum<DT, 512><<<L.acc_grid, 512, L.acc_smem, st>>>(b, r, b.plan_acc);
     kb_bc_partial<<<nsm * L.bc_ctas, 256, 0, st>>>(b, r, b.plan_bc);
     kb_bc_finish<<<nsm * 2, 256, 0, st>>>(b, r, +1.0);
     if (L.pair_classes) batch_pair_launches(b, L, r, sizeof(DT), st);
@@ -380,12 +384,19 @@ void batch_config(BatchLaunch& L, int dbytes, int n_max, int64_t cap_max) {
     L.mask_in_smem = base + mb <= limit ? 1 : 0;
     L.acc_smem = (int)(L.mask_in_smem ? base + mb : base);
     int per_sm = 1;
+    if (L.acc_threads != 128 && L.acc_threads != 256 && L.acc_threads != 512) L.acc_threads = kAccThreadsNarrow;
+    auto occ = [&](auto kern, int threads) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, L.acc_smem);
+    };
     if (dbytes == 4) {
-        cudaFuncSetAttribute(kb_accum<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_accum<int32_t>, kAccThreadsNarrow, L.acc_smem);
+        if (L.acc_threads == 128) occ(kb_accum<int32_t, 128>, 128);
+        else if (L.acc_threads == 256) occ(kb_accum<int32_t, 256>, 256);
+        else occ(kb_accum<int32_t, 512>, 512);
     } else {
-        cudaFuncSetAttribute(kb_accum<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_accum<int64_t>, kAccThreadsNarrow, L.acc_smem);
+        if (L.acc_threads == 128) occ(kb_accum<int64_t, 128>, 128);
+        else if (L.acc_threads == 256) occ(kb_accum<int64_t, 256>, 256);
+        else occ(kb_accum<int64_t, 512>, 512);
     }
     if (per_sm < 1) per_sm = 1;
     if (L.acc_per_sm > 0) per_sm = std::min(per_sm, L.acc_per_sm);

@@ -98,7 +98,8 @@ def test_batch_stops_a_graph_at_its_invalid_update():
 def test_batch_tiles_do_not_change_results():
     fam = _family(6, 33, nlo=50, nhi=200)
     outs = []
-    for tiles in ([4, 8, 8, 0], [1, 2, 1, 1], [4, 8, 8, 0, 1, 0], [4, 8, 8, 0, 8, 1], [2, 4, 4, 1, 2, 1]):
+    for tiles in ([4, 8, 8, 0], [1, 2, 1, 1], [4, 8, 8, 0, 1, 0], [4, 8, 8, 0, 8, 1], [2, 4, 4, 1, 2, 1],
+                  [4, 8, 8, 0, 4, 0, 256], [2, 8, 16, 1, 2, 1, 256], [4, 8, 8, 0, 4, 0, 128]):
         graphs = [binding.BCGraph(g) for g, _ in fam]
         batch = binding.BCBatch(graphs)
         batch.bc_batch_set_tiles(tiles)
