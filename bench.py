@@ -12,8 +12,9 @@ re-accumulation of every changed source, BC update).  Reported:
   value  updates/s, device time (CUDA events on the library's stream) of K steps whose
          update batch is already staged in device memory;
   e2e    the same K steps through the public C-ABI call with host buffers (one
-         bc_apply_updates call per update, so p50/p99 latency per update), plus a
-         read of the BC vector after each step;
+         bc_apply_updates call per step, the updates copied to the device inside the
+         call), plus a read of the BC vector after each step; p50/p99 latency per
+         update and the rate of one synchronous call per update from a second pass;
   roofline of the dominant kernel class (events around each launch, second pass over
          further steps), the GPU full-recompute baseline (bc_init_static on the final
          graph) and the CPU oracle on a bounded sample of sources.
@@ -452,7 +453,13 @@ def run_ours(args):
                          "per_update": per_upd}
     A.close()
 
-    # ---------------- e2e through the C-ABI with host buffers, per-update latency
+    # ---------------- e2e through the C-ABI with host buffers
+    # Timed pass: every step is one bc_apply_updates call with the step's updates in host
+    # memory (copied to the device inside the call) and a read of the BC vector after it,
+    # on a fresh handle brought to the same state by the warm-up steps.  Latency pass: the
+    # same steps on another fresh handle, one call per update, timed around each call
+    # (p50/p99 per update, and the rate of that synchronous use), with the device time of
+    # every update from events around its call for the per-class rates.
     e2e = None
     per_class = None
     lat = []
@@ -461,40 +468,53 @@ def run_ours(args):
         for i in range(W):
             rc, _ = B.bc_apply_updates(sl[i])
             assert rc == 0
-        barrier()
-        h2d = 0
+        enc = [binding.encode_updates(s) for s in sl[W:W + K]]
+        h2d = sum(rec.nbytes + ed.nbytes for rec, ed in enc)
         d2h = 0
-        # device time of every update (events on the library's stream around its call)
-        # and its class, for the per-class rates
-        evs = []
-        kinds = []
+        barrier()
         t0 = time.perf_counter()
-        for s in sl[W:W + K]:
-            for up in s:
-                rec, ed = binding.encode_updates([up])
-                h2d += rec.nbytes + ed.nbytes
-                d2h += 4
-                ea = torch.cuda.Event(enable_timing=True)
-                eb = torch.cuda.Event(enable_timing=True)
-                noop0 = B.bc_get_info()["noop_updates"]
-                ta = time.perf_counter()
-                ea.record(stream)
-                rc, _ = B.bc_apply_updates((rec, ed))
-                eb.record(stream)
-                lat.append(1e3 * (time.perf_counter() - ta))
-                assert rc == 0, B.last_error()
-                evs.append((ea, eb))
-                kinds.append((up[0], B.bc_get_info()["noop_updates"] > noop0))
+        for rec, ed in enc:
+            rc, _ = B.bc_apply_updates((rec, ed))
+            assert rc == 0, B.last_error()
             scores = B.bc_get_scores()
             d2h += 2 * scores.nbytes
         barrier()
         wall = max_over_ranks(time.perf_counter() - t0, dist)
+        B.close()
+        C = binding.BCGraph(g, dist=dtype, stream=stream.cuda_stream)
+        for i in range(W):
+            rc, _ = C.bc_apply_updates(sl[i])
+            assert rc == 0
+        evs = []
+        kinds = []
+        call_s = 0.0
+        for s in sl[W:W + K]:
+            for up in s:
+                rec, ed = binding.encode_updates([up])
+                ea = torch.cuda.Event(enable_timing=True)
+                eb = torch.cuda.Event(enable_timing=True)
+                noop0 = C.bc_get_info()["noop_updates"]
+                ta = time.perf_counter()
+                ea.record(stream)
+                rc, _ = C.bc_apply_updates((rec, ed))
+                eb.record(stream)
+                dt = time.perf_counter() - ta
+                lat.append(1e3 * dt)
+                call_s += dt
+                assert rc == 0, C.last_error()
+                evs.append((ea, eb))
+                kinds.append((up[0], C.bc_get_info()["noop_updates"] > noop0))
+            ta = time.perf_counter()
+            C.bc_get_scores()
+            call_s += time.perf_counter() - ta
         dev = [ea.elapsed_time(eb) for ea, eb in evs]
         e2e = {"value": job_rate(len(timed), world, wall), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                "d2h_bytes_per_step": d2h // K, "p50_ms": float(np.percentile(lat, 50)),
-               "p99_ms": float(np.percentile(lat, 99))}
+               "p99_ms": float(np.percentile(lat, 99)),
+               "calls": "one bc_apply_updates per step; p50/p99 from one call per update",
+               "per_update_calls_value": len(timed) / call_s}
         per_class = per_class_rates(dev, kinds)
-        B.close()
+        C.close()
 
     # ---------------- complete graph: the "effective decreases" variant (w' <= d(u,v),
     # d read from the handle's own state through the C-ABI), per-update device times

@@ -79,6 +79,7 @@ struct bc_graph {
     double last_init_ms = 0.0;
     int64_t walk_cap_alloc = 0;   // entries allocated for the DAG walks' buffer
     std::vector<void*> allocs;
+    std::vector<void*> allocs_async;   // stream-ordered (replaced while the handle lives)
     // launch accounting and optional per-class event timing
     int64_t launches = 0;
     bool profile = false;
@@ -128,6 +129,28 @@ void dfree(bc_graph* g, void* p) {
     auto it = std::find(g->allocs.begin(), g->allocs.end(), p);
     if (it != g->allocs.end()) g->allocs.erase(it);
     cudaFree(p);
+}
+
+// Stream-ordered allocation for the buffers that are replaced while the handle lives
+// (the E* arrays, their keep flags, the accumulation work space): cudaFree waits for
+// the whole device, the work of every other handle included, while a free ordered on
+// this handle's stream waits only for this handle's earlier work.
+template <typename T>
+int dalloc_async(bc_graph* g, T** p, size_t count) {
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), bytes, g->d.st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMallocAsync");
+    g->allocs_async.push_back(*p);
+    g->bytes += (int64_t)bytes;
+    return BC_OK;
+}
+
+void dfree_async(bc_graph* g, void* p) {
+    if (!p) return;
+    auto it = std::find(g->allocs_async.begin(), g->allocs_async.end(), p);
+    if (it != g->allocs_async.end()) g->allocs_async.erase(it);
+    cudaFreeAsync(p, g->d.st);
 }
 
 int status_of_err(int32_t f) {
@@ -214,15 +237,15 @@ int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<i
     Dev& d = g->d;
     const size_t asz = g->dbytes == 4 ? sizeof(Arc<int32_t>) : sizeof(Arc<int64_t>);
     if (cap + cap / 8 > d.e_cap) {
-        dfree(g, d.e_src);
-        dfree(g, d.e_arc);
+        dfree_async(g, d.e_src);
+        dfree_async(g, d.e_arc);
         d.e_src = nullptr;
         d.e_arc = nullptr;
         const int64_t ncap = cap + cap / 4 + 64;
         int rc;
-        if ((rc = dalloc(g, &d.e_src, ncap))) return rc;
+        if ((rc = dalloc_async(g, &d.e_src, ncap))) return rc;
         unsigned char* p = nullptr;
-        if ((rc = dalloc(g, &p, ncap * asz))) return rc;
+        if ((rc = dalloc_async(g, &p, ncap * asz))) return rc;
         d.e_arc = p;
         d.e_cap = ncap;
     }
@@ -258,10 +281,10 @@ int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<i
     accum_config(d);
     const int64_t need = (int64_t)d.acc_grid * d.ws_stride;
     if (need > g->ws_cap) {
-        dfree(g, d.ws);
+        dfree_async(g, d.ws);
         d.ws = nullptr;
         int rc;
-        if ((rc = dalloc(g, &d.ws, need))) return rc;
+        if ((rc = dalloc_async(g, &d.ws, need))) return rc;
         g->ws_cap = need;
     }
     return BC_OK;
@@ -274,9 +297,9 @@ int estar_rebuild(bc_graph* g, const std::vector<HArc>& pending) {
     if (rc) return rc;
     Dev& d = g->d;
     if (d.e_cap > g->d_keep_cap) {
-        dfree(g, g->d_keep);
+        dfree_async(g, g->d_keep);
         g->d_keep = nullptr;
-        if ((rc = dalloc(g, &g->d_keep, d.e_cap))) return rc;
+        if ((rc = dalloc_async(g, &g->d_keep, d.e_cap))) return rc;
         g->d_keep_cap = d.e_cap;
     }
     launch_estar_keep(d, g->d_keep);
@@ -569,6 +592,9 @@ void destroy_all(bc_graph* g) {
     }
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
+    for (void* p : g->allocs_async) cudaFreeAsync(p, g->d.st);
+    if (!g->allocs_async.empty()) cudaStreamSynchronize(g->d.st);
+    g->allocs_async.clear();
     for (void* p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->h_err) cudaFreeHost(g->h_err);
@@ -1538,6 +1564,7 @@ int bc_batch_apply(bc_batch* b, const int32_t* n_updates, const bc_update* ups, 
     BatchArgs& a = b->args;
     a.G = G;
     a.mask_in_smem = b->L.mask_in_smem;
+    a.n_max = b->n_max;
     a.devs = b->d_devs;
     a.upd = b->d_upd;
     a.entries = b->d_entries;

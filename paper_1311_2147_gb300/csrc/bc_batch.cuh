@@ -26,6 +26,7 @@ struct BatchEOp {
 struct BatchArgs {
     int32_t G;
     int32_t mask_in_smem;
+    int32_t n_max;            // largest n of the batch
     const Dev* devs;          // [G]
     const BatchUpd* upd;      // [rounds * G]
     const VEdge* entries;

@@ -351,6 +351,10 @@ __device__ __forceinline__ int64_t item_weight(int T, int tcap) { return (T == 0
 // bucket with one shared-memory atomic), then each warp scans a contiguous run of the
 // sorted rows and one block scan joins the runs.
 // Also adds the rows with a correction and their targets to stats[8], stats[9].
+// Listed rows the weights pass stages in shared memory (up to n; none past the limit).
+constexpr int kWeightsStageMax = 20480;   // 160 KB of row ids and counts
+static int weights_stage(int n) { return n <= kWeightsStageMax ? n : 0; }
+
 struct PairWeightsSmem {
     int64_t wsum[32];
     int64_t s_total;
@@ -358,11 +362,16 @@ struct PairWeightsSmem {
     int s_hist[kPairCap + 1];
 };
 
-// (CTA-wide, 1024 threads.)
+// (CTA-wide, 1024 threads.)  s_r and s_T: scap ints each of shared memory; when the
+// listed rows fit, they and their target counts are staged there first, every load
+// issued before any is used (the passes below would otherwise wait on a row id and then
+// on its count, tile after tile).  The sorted rows' counts are staged in wpre, which
+// the last pass overwrites with the prefix.
 __device__ __forceinline__ void dev_pair_weights(const int32_t* rows, const int32_t* count, const int32_t* tcnt,
                                                  int tcap, int nchunks, int32_t* prows, int32_t* pcount,
                                                  int64_t* wpre, int64_t* stats, int32_t* next_piece,
-                                                 int32_t* walk_ctl, int32_t* walk_rowE, PairWeightsSmem& sm) {
+                                                 int32_t* walk_ctl, int32_t* walk_rowE, PairWeightsSmem& sm,
+                                                 int32_t* s_r, int32_t* s_T, int scap) {
     int64_t* wsum = sm.wsum;
     int64_t& s_total = sm.s_total;
     int64_t* s_rows = sm.s_rows;
@@ -376,10 +385,16 @@ __device__ __forceinline__ void dev_pair_weights(const int32_t* rows, const int3
     // items are handed out first and the light ones fill the end of the kernel.  The
     // order inside a bucket follows the atomics; a row's result does not depend on it.
     for (int b = tid; b <= kPairCap; b += blockDim.x) s_hist[b] = 0;
+    const bool staged = cnt_all <= scap;
+    if (staged) {
+        for (int i = tid; i < cnt_all; i += blockDim.x) s_r[i] = rows[i];
+        __syncthreads();
+        for (int i = tid; i < cnt_all; i += blockDim.x) s_T[i] = tcnt[s_r[i]];
+    }
     __syncthreads();
     for (int i0 = 0; i0 < cnt_all; i0 += blockDim.x) {   // warp-uniform bounds (the match)
         const int i = i0 + tid;
-        const int T = i < cnt_all ? tcnt[rows[i]] : 0;
+        const int T = i < cnt_all ? (staged ? s_T[i] : tcnt[rows[i]]) : 0;
         const bool ok = T > 0 && T <= tcap;
         const unsigned peers = __match_any_sync(0xffffffffu, ok ? T : -1);
         if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[T], __popc(peers));
@@ -401,15 +416,19 @@ __device__ __forceinline__ void dev_pair_weights(const int32_t* rows, const int3
         for (int i = tid; i < cnt_all; i += blockDim.x) walk_rowE[i] = 0;
     for (int i0 = 0; i0 < cnt_all; i0 += blockDim.x) {
         const int i = i0 + tid;
-        const int r = i < cnt_all ? rows[i] : 0;
-        const int T = i < cnt_all ? tcnt[r] : 0;
+        const int r = i < cnt_all ? (staged ? s_r[i] : rows[i]) : 0;
+        const int T = i < cnt_all ? (staged ? s_T[i] : tcnt[r]) : 0;
         const bool ok = T > 0 && T <= tcap;
         const unsigned peers = __match_any_sync(0xffffffffu, ok ? T : -1);
         const int leader = __ffs(peers) - 1;
         int p0 = 0;
         if (ok && lane == leader) p0 = atomicAdd(&s_hist[T], __popc(peers));
         p0 = __shfl_sync(0xffffffffu, p0, leader);
-        if (ok) prows[p0 + __popc(peers & below)] = r;
+        if (ok) {
+            const int pos = p0 + __popc(peers & below);
+            prows[pos] = r;
+            wpre[pos] = T;
+        }
     }
     __syncthreads();
     int64_t my_rows = 0, my_tgts = 0;
@@ -427,7 +446,7 @@ __device__ __forceinline__ void dev_pair_weights(const int32_t* rows, const int3
     int64_t run = 0;
     for (int b0 = w0; b0 < w1; b0 += 32) {
         const int i = b0 + lane;
-        const int64_t iw = i < w1 ? item_weight(tcnt[prows[i]], tcap) : 0;
+        const int64_t iw = i < w1 ? item_weight((int)wpre[i], tcap) : 0;
         if (iw) {
             ++my_rows;
             my_tgts += iw - 1;
@@ -446,7 +465,7 @@ __device__ __forceinline__ void dev_pair_weights(const int32_t* rows, const int3
     run = wsum[wid];
     for (int b0 = w0; b0 < w1; b0 += 32) {
         const int i = b0 + lane;
-        const int64_t x = i < w1 ? item_weight(tcnt[prows[i]], tcap) * nchunks : 0;
+        const int64_t x = i < w1 ? item_weight((int)wpre[i], tcap) * nchunks : 0;
         const int64_t incl = warp_incl(x);
         if (i < w1) wpre[i] = run + incl - x;
         run += __shfl_sync(0xffffffffu, incl, 31);
@@ -481,12 +500,14 @@ __global__ void __launch_bounds__(1024) k_pair_weights(const int32_t* rows, cons
                                                        const int32_t* tcnt, int tcap, int nchunks,
                                                        int32_t* prows, int32_t* pcount,
                                                        int64_t* wpre, int64_t* stats, int32_t* next_piece,
-                                                       int32_t* walk_ctl, int32_t* walk_rowE, const int32_t* err) {
+                                                       int32_t* walk_ctl, int32_t* walk_rowE, const int32_t* err,
+                                                       int scap) {
     pdl_enter();
     __shared__ PairWeightsSmem sm;
+    extern __shared__ int32_t s_stage[];   // 2 * scap ints
     if (*err) return;
     dev_pair_weights(rows, count, tcnt, tcap, nchunks, prows, pcount, wpre, stats, next_piece, walk_ctl, walk_rowE,
-                     sm);
+                     sm, s_stage, s_stage + scap, scap);
 }
 
 // Queue of one warp's matches: entry = lane (5 bits) | q (3) | target index u (7) |
@@ -840,15 +861,16 @@ __global__ void __launch_bounds__(kPlanThreads) kb_pair_plan(BatchArgs b) {
 
 // One CTA per graph in turn: rows most targets first and their weight prefix
 // (k_pair_weights), with the graph's own columns per thread.
-__global__ void __launch_bounds__(1024) kb_pair_weights(BatchArgs b, int r) {
+__global__ void __launch_bounds__(1024) kb_pair_weights(BatchArgs b, int r, int scap) {
     __shared__ PairWeightsSmem sm;
+    extern __shared__ int32_t s_stage[];   // 2 * scap ints
     for (int g = blockIdx.x; g < b.G; g += gridDim.x) {
         if (!batch_pair_graph(b, r, g)) continue;   // block-uniform
         const Dev& d = b.devs[g];
         const int cw = kPairThreads * pair_vn(d.dbytes, d.n);
         const int nchunks = (d.n + cw - 1) / cw;
         dev_pair_weights(d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows, d.counts + 5, d.pair_w,
-                         d.stats, d.counts + 4, nullptr, nullptr, sm);
+                         d.stats, d.counts + 4, nullptr, nullptr, sm, s_stage, s_stage + scap, scap);
         __syncthreads();
     }
 }
@@ -988,7 +1010,8 @@ static void batch_pairs(const BatchArgs& b, const BatchLaunch& L, int r, cudaStr
     const int G = b.G, nsm = L.nsm;
     batch_plan(b, r, 3, 2, b.plan_pr, L.scan_unroll, st);
     kb_pair_plan<DT><<<nsm * 8, kPlanThreads, 0, st>>>(b);
-    kb_pair_weights<<<std::min(G, nsm * 2), 1024, 0, st>>>(b, r);
+    const int scap = weights_stage(b.n_max);
+    kb_pair_weights<<<std::min(G, nsm * 2), 1024, 2 * sizeof(int32_t) * (size_t)scap, st>>>(b, r, scap);
     const int pgrid = nsm * kPairCtasPerSm;
     for (int c = 0; c < kPairClasses; ++c) {
         if (!((L.pair_classes >> c) & 1)) continue;
@@ -1444,6 +1467,10 @@ int64_t walk_warps(int nsm) { return (int64_t)nsm * kWalkCtasPerSm * kWalkWarps;
 int64_t walk_ctas(int nsm) { return (int64_t)nsm * kWalkRowCtasPerSm; }
 
 cudaError_t walk_setup() {
+    const int wmax = 2 * (int)sizeof(int32_t) * kWeightsStageMax;
+    cudaError_t e0 = cudaFuncSetAttribute(k_pair_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax);
+    if (e0 == cudaSuccess) e0 = cudaFuncSetAttribute(kb_pair_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax);
+    if (e0 != cudaSuccess) return e0;
     cudaError_t e = cudaFuncSetAttribute(k_walk_units<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kWalkSmemMax);
     if (e == cudaSuccess)
@@ -1483,9 +1510,10 @@ void launch_pairdep(const Dev& d, const WalkUpd* upd) {
     const int vn = pair_vn(d.dbytes, d.n);
     const int cw = kPairThreads * vn;
     const int nchunks = (d.n + cw - 1) / cw;
-    launch_k(k_pair_weights, 1, 1024, 0, d.st, d.acc_rows, d.counts + 1, d.tcnt, d.tcap, nchunks, d.pair_rows,
-                                          d.counts + 5, d.pair_w, d.stats, d.counts + 4, upd ? d.walk_ctl : nullptr,
-                                          upd ? d.walk_rowE : nullptr, d.err);
+    const int scap = weights_stage(d.n);
+    launch_k(k_pair_weights, 1, 1024, 2 * sizeof(int32_t) * (size_t)scap, d.st, d.acc_rows, d.counts + 1, d.tcnt,
+             d.tcap, nchunks, d.pair_rows, d.counts + 5, d.pair_w, d.stats, d.counts + 4,
+             upd ? d.walk_ctl : nullptr, upd ? d.walk_rowE : nullptr, d.err, scap);
     if (upd) {
         if (d.dbytes == 4) launch_walks<int32_t>(d, *upd, nchunks, vn);
         else launch_walks<int64_t>(d, *upd, nchunks, vn);
