@@ -165,7 +165,7 @@ def test_estar_segment_moves_and_rebuilds():
         em = synth.EdgeMap.of(g)
         rng = synth.Rng(44 + directed)
         ups = []
-        for i in range(14):
+        for i in range(40):
             v = int(rng.below(g.n, 1)[0])
             nb = [int(x) for x in rng.below(g.n, 24) if int(x) != v]
             seen, edges = set(), []
