@@ -220,11 +220,8 @@ int sync_check(bc_graph* g) {
     return BC_OK;
 }
 
-// Lay the E* superset out with slack per vertex and upload it.  The device arrays hold
-// twice the slots the layout needs (at least half as many again after a re-layout that
-// keeps them): the free region where full segments move, so that re-layouts -- a
-// host-side rebuild that holds up the caller, and in the server every other graph's
-// dispatch -- stay rare.
+// Lay the E* superset out with slack per vertex and upload it.  The device arrays get
+// a quarter more slots than the layout needs: the free region where full segments move.
 int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<int32_t>* extra = nullptr) {
     const int32_t n = g->n;
     std::vector<int32_t> deg(n, 0);
@@ -239,12 +236,12 @@ int estar_layout(bc_graph* g, const std::vector<HArc>& arcs, const std::vector<i
     const int64_t cap = g->e_off[n];
     Dev& d = g->d;
     const size_t asz = g->dbytes == 4 ? sizeof(Arc<int32_t>) : sizeof(Arc<int64_t>);
-    if (cap + cap / 2 > d.e_cap) {
+    if (cap + cap / 8 > d.e_cap) {
         dfree_async(g, d.e_src);
         dfree_async(g, d.e_arc);
         d.e_src = nullptr;
         d.e_arc = nullptr;
-        const int64_t ncap = 2 * cap + 64;
+        const int64_t ncap = cap + cap / 4 + 64;
         int rc;
         if ((rc = dalloc_async(g, &d.e_src, ncap))) return rc;
         unsigned char* p = nullptr;

@@ -334,6 +334,8 @@ void launch_pairdep(const Dev& d, const WalkUpd* upd);   // upd: DAG walks (k_pa
 size_t walk_smem(int n);
 int64_t walk_warps(int nsm);
 int64_t walk_ctas(int nsm);
+// Kernel attributes of the pair corrections (the walks' and the weights pass's dynamic
+// shared memory limits); bc_init_static sets them before it builds a handle.
 cudaError_t walk_setup();
 void launch_pair_clear(const Dev& d);
 void launch_bc_fix(const Dev& d);

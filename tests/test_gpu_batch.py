@@ -121,3 +121,31 @@ def test_batch_config_shape_sample():
     for (g, ups), m in zip(fam, graphs):
         gg = synth.apply_updates(g, ups)
         compare_rows(m, gg, [0, g.n // 2, g.n - 1], label=f"batch workload n={g.n}")
+
+
+def test_batch_pair_classes_int32():
+    # int32 distances: the batched column test runs once per class of columns per
+    # thread (8 where n is a multiple of 8, 4 where of 4, else 1); graphs of every class
+    # in one batch, each bit for bit its result alone and matching the oracle
+    ns = [64, 100, 101, 136, 77, 200]
+    fam = []
+    for i, n in enumerate(ns):
+        g = synth.barabasi_albert(n, 3, 1, 30, 500 + i)
+        ups = synth.update_stream(g, 3, 3, 2, 600 + i, 1, 30, kmin=1, kmax=4)
+        fam.append((g, ups))
+    alone = []
+    for g, ups in fam:
+        a = binding.BCGraph(g, dist="i32")
+        rc, done = a.bc_apply_updates(ups)
+        assert rc == 0 and done == len(ups)
+        alone.append(a)
+    mixed = [binding.BCGraph(g, dist="i32") for g, _ in fam]
+    batch = binding.BCBatch(mixed)
+    rc, done = batch.bc_batch_apply([ups for _, ups in fam])
+    assert rc == 0, batch.last_error()
+    for (g, ups), a, m in zip(fam, alone, mixed):
+        for x, y in zip(a.bc_get_rows(), m.bc_get_rows()):
+            assert np.array_equal(x, y), f"n={g.n}"
+        assert np.array_equal(a.bc_get_scores(), m.bc_get_scores()), f"n={g.n}"
+        compare_full(m, synth.apply_updates(g, ups), label=f"int32 batch n={g.n}")
+    assert sum(m.bc_get_info()["pair_rows"] for m in mixed) > 0
