@@ -592,6 +592,12 @@ void destroy_all(bc_graph* g) {
     }
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->d.st3) {
+        cudaStreamSynchronize(g->d.st3);
+        cudaStreamDestroy(g->d.st3);
+    }
+    if (g->d.ev3_fork) cudaEventDestroy(g->d.ev3_fork);
+    if (g->d.ev3_join) cudaEventDestroy(g->d.ev3_join);
     for (void* p : g->allocs_async) cudaFreeAsync(p, g->d.st);
     if (!g->allocs_async.empty()) cudaStreamSynchronize(g->d.st);
     g->allocs_async.clear();
@@ -740,7 +746,10 @@ int bc_init_static(bc_graph** out, int32_t n, int64_t m, const int32_t* src, con
         cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess ||
         (!dir && (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
                   cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                  cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess))) {
+                  cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaStreamCreateWithFlags(&g->d.st3, cudaStreamNonBlocking) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&g->d.ev3_fork, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&g->d.ev3_join, cudaEventDisableTiming) != cudaSuccess))) {
         destroy_all(g);
         return fail(nullptr, BC_ERR_OOM, "pinned host allocation, stream or event creation failed");
     }

@@ -216,6 +216,10 @@ struct Dev {
     int64_t* bcfix;      // [2n] BC change of the corrected rows in this update, per column a
                          // fixed-point pair (units of 2^-24, units of 2^-56); zero between updates
     cudaStream_t st;
+    // a third stream for the heaviest rows of the DAG walks' phase 2 (undirected graphs):
+    // forked from st after the walks, joined back before the BC fix-up
+    cudaStream_t st3;
+    cudaEvent_t ev3_fork, ev3_join;
 };
 
 constexpr int kRowsPerBlock = 64;   // rows per partial sum of the BC reduction

@@ -1485,9 +1485,20 @@ static void launch_walks(const Dev& d, const WalkUpd& upd, int nchunks, int vn) 
     WalkArgs<DT> w{d.e_off, d.e_len, (const Arc<DT>*)d.e_arc, d.walk_list, d.walk_buf, d.walk_cap, d.walk_useg,
                    d.walk_acc2, d.walk_tl, d.walk_ctl, d.walk_rowE, d.stats, nchunks, upd};
     launch_k(k_walk_units<DT>, grid, kWalkThreads, walk_smem(d.n), d.st, pair_args<DT>(d), w);
-    launch_k(k_walk_rows<DT>, rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), d.st, pair_args<DT>(d), w);
+    // phase 2: the heaviest rows (a few CTAs with a long tail) on the third stream beside
+    // the two hash-table classes (disjoint rows, their own counters and scratch)
+    const bool third = d.st3 != nullptr;
+    cudaStream_t sr = d.st;
+    if (third) {
+        cudaEventRecord(d.ev3_fork, d.st);
+        cudaStreamWaitEvent(d.st3, d.ev3_fork, 0);
+        sr = d.st3;
+    }
+    launch_k(k_walk_rows<DT>, rgrid, kWalkThreads, (size_t)((d.n + 31) / 32) * sizeof(uint32_t), sr, pair_args<DT>(d), w);
+    if (third) cudaEventRecord(d.ev3_join, d.st3);
     launch_k(k_walk_rows_hash<DT, WalkLight>, d.nsm * WalkLight::ctas, WalkLight::threads, WalkLight::smem, d.st, pair_args<DT>(d), w);
     launch_k(k_walk_rows_hash<DT, WalkMid>, d.nsm * WalkMid::ctas, WalkMid::threads, WalkMid::smem, d.st, pair_args<DT>(d), w);
+    if (third) cudaStreamWaitEvent(d.st, d.ev3_join, 0);
     // the column test, which does nothing unless the walks' buffer overflowed
     PairArgs<DT> a = pair_args<DT>(d);
     a.gate = d.walk_ctl + 4;
