@@ -342,9 +342,14 @@ int bc_static_scores_noalloc(int32_t n, int64_t arcs, const int32_t* d_off, cons
  * that has one; within a round each phase of the update (Algorithm 4 and Lemma 2 / 4 in
  * both directions, DAG rebuild, Kahn order, Eq. 4, BC) runs as one kernel over the work
  * of all graphs at once, and the rounds are captured once into a CUDA graph that is
- * replayed by one graph launch per call.  A graph's result is bit-identical to applying
- * the same updates to it alone.  The graphs must share the distance type; they stay
- * owned by the caller and must not be used by other calls while a batch call runs.
+ * replayed by one graph launch per call.  Undirected graphs with pair corrections on
+ * (option "pair_updates", the default) re-accumulate only their rows over the target
+ * cap and correct the others pair by pair with the column test; the DAG walks are not
+ * used in batches.  A graph's result is bit-identical to applying the same updates to it
+ * alone with the same options (for an undirected graph alone: the column test, i.e. n
+ * below the walks' default or "pair_walk" 0; with the walks the dependencies agree
+ * within rounding).  The graphs must share the distance type; they stay owned by the
+ * caller and must not be used by other calls while a batch call runs.
  */
 typedef struct bc_batch bc_batch;
 
